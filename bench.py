@@ -1,0 +1,342 @@
+"""Benchmark: explicit f-x poststack depth migration on GB300.
+
+Metric: extrapolated points x frequencies per second, Nx * Nz * Nw / t, where t
+is the CUDA-event time of one depth loop (fxmig_migrate, all depth rows) plus
+the imaging reduction (fxmig_image).  Workload: the 2048-trace layered medium
+with dipping interfaces and a smoothed lens (Nx=2048, dx=12.5 m, Nt=2000,
+dt=2 ms, Nz=800, dz=5 m, 5-60 Hz -> 221 frequencies, 25-tap operators, 1024
+table entries); the input section is synthetic (seeded) and stands in for the
+SEG/EAGE salt data the paper migrates, which is not available.
+
+One JSON line on stdout (rank 0).  `--impl reference` times the FP64 CPU
+oracle instead (the only other place this script runs the oracle is the
+`cpu_baseline` leg).  Under torchrun every rank migrates its own, independently
+seeded line (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {w.name: w for w in (W.DIFFRACTOR_128, W.LAYERED_LENS_2048, W.LARGE_8192)}
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+NOMINAL_SMS = 152
+NOMINAL_SM_MHZ = 2070.0
+
+
+def flops_per_point(L: int) -> int:
+    """Algorithmic FP32 flops per extrapolated point x frequency (Eq. 1 with
+    symmetric taps): L complex pair additions (2L), one complex product (6),
+    L complex multiply-adds (8L), the imaging addition (1) and the table-index
+    product (1): 10L + 8."""
+    return 10 * L + 8
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            self.proc = subprocess.Popen([exe, f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(w: W.Workload, seed: int):
+    v, refl = W.layered_lens_model(w, seed=seed)
+    sec = W.normal_incidence_section(w, v, refl, seed=seed)
+    vm = (0.5 * v).astype(np.float32)            # exploding-reflector migration velocity
+    return sec.astype(np.float32), vm
+
+
+def k_max_of(w: W.Workload, vm_min: float) -> float:
+    return 2.0 * math.pi * (w.i0 + w.nw - 1) / (w.nt * w.dt) / vm_min
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": NOMINAL_SM_MHZ}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_run(w: W.Workload, sec, vm, threads: int = 0):
+    """FP64 oracle migration of the whole workload; returns (seconds of the
+    depth loop, final wavefield, image, cores used)."""
+    import oracle as O
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    kmax = float(om[-1] / float(vm.min()))
+    table = O.design_operators(w.nk, kmax, w.dx, w.dz, w.L, w.theta_deg)
+    _, dk = O.k_grid(w.nk, kmax)
+    P0 = O.band_dft(sec.astype(np.float64), w.i0, w.nw)
+    cores = threads or O.max_threads()
+    t0 = time.perf_counter()
+    P, img = O.migrate(P0, vm, table, O.q_values(om, dk), nthreads=cores)
+    return time.perf_counter() - t0, P, img, cores
+
+
+def run_reference(args, w):
+    """The oracle on the host cores, same metric and workload; each step is a
+    bounded sample: a contiguous block of frequencies over the full line and
+    all depth rows (the cost per point x frequency does not depend on which
+    frequencies are taken)."""
+    import oracle as O
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    sec, vm = make_inputs(w, w.seed)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    kmax = float(om[-1] / float(vm.min()))
+    table = O.design_operators(w.nk, kmax, w.dx, w.dz, w.L, w.theta_deg)
+    _, dk = O.k_grid(w.nk, kmax)
+    nws = min(w.nw, args.ref_freqs)
+    j0 = (w.nw - nws) // 2
+    P0 = O.band_dft(sec.astype(np.float64), w.i0 + j0, nws)
+    q = O.q_values(om[j0:j0 + nws], dk)
+    cores = O.max_threads()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.migrate(P0, vm, table, q, nthreads=cores)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    pts = w.nx * w.nz * nws
+    val = pts * len(times) / tot
+    line = {"impl": "reference", "metric": "extrapolated points*freq/s (Nx*Nz*Nw/s)", "value": val,
+            "unit": "point*freq/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered+lens model)",
+            "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "nw": w.nw, "L": w.L},
+            "cpu_baseline": {"value": val, "unit": "point*freq/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nws} of {w.nw} frequencies (bins {w.i0 + j0}..{w.i0 + j0 + nws - 1}), "
+                                       f"all {w.nx} traces and {w.nz} depth rows per step"},
+            "e2e": {"value": val, "unit": "point*freq/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_native(args, w):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1912_05529_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1912_05529_gb300 as fx
+
+    seed = w.seed + 1000 * rank
+    sec, vm = make_inputs(w, seed)
+    d = fx.Desc(nx=w.nx, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz, dt=w.dt,
+                theta_max_deg=w.theta_deg, k_max=k_max_of(w, float(vm.min())))
+    launch = fx.Launch(mode=args.mode, cluster=args.cluster, groups=args.groups, warps=args.warps)
+    b = fx.allocate(d, launch)
+    b.section.copy_(torch.from_numpy(sec))
+    b.vel.copy_(torch.from_numpy(vm))
+    fx.fxmig_design_operators(d, b.table)
+    fx.fxmig_t2f(d, b.section, b.slab, b.ws_t2f)
+    slab0 = b.slab.clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fx.fxmig_migrate_ex(d, launch, b.slab, b.vel, b.table, b.partials, 0, d.nz, b.ws_mig)
+        fx.fxmig_image(d, b.partials, b.image)
+
+    for _ in range(args.warmup):
+        b.slab.copy_(slab0)
+        step()
+    torch.cuda.synchronize()
+    if fx.fxmig_check(b.ws_mig) != fx.FXMIG_OK:
+        raise RuntimeError("device status after warm-up: " + fx.fxmig_strerror(fx.fxmig_check(b.ws_mig)))
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        for e0, e1, e2 in ev:
+            b.slab.copy_(slab0)
+            flush.fill_(1)
+            e0.record(stream)
+            fx.fxmig_migrate_ex(d, launch, b.slab, b.vel, b.table, b.partials, 0, d.nz, b.ws_mig)
+            e1.record(stream)
+            fx.fxmig_image(d, b.partials, b.image)
+            e2.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    mig_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * w.points * args.steps / (tot_ms * 1e-3)
+
+    # end to end through the public call with host buffers (pinned)
+    sec_h = torch.from_numpy(sec).pin_memory()
+    vm_h = torch.from_numpy(vm).pin_memory()
+    img_h = torch.empty((d.nz, d.nx), dtype=torch.float32, pin_memory=True)
+    for _ in range(2):
+        fx.migrate_section(d, sec_h, vm_h, b, launch, img_h, design=False)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fx.migrate_section(d, sec_h, vm_h, b, launch, img_h, design=False)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_val = world * w.points * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", NOMINAL_SM_MHZ))
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    mig_avg = sum(mig_ms) / len(mig_ms)
+    achieved = flops_per_point(w.L) * w.points / (mig_avg * 1e-3) / 1e12
+    nparts = b.partials.shape[0]
+    line = {
+        "metric": "extrapolated points*freq/s (Nx*Nz*Nw/s)", "value": value, "unit": "point*freq/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered+lens model, normal-incidence section)",
+        "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "nw": w.nw, "L": w.L, "nk": w.nk,
+                   "mode": "persistent" if args.mode != 2 else "per_depth",
+                   "l2": "flushed between steps (256 MiB write)", "partials": nparts,
+                   "parallelism": f"{world} independent lines" if world > 1 else "1 line"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_migrate_persistent" if args.mode != 2 else "k_migrate_step",
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz ({peak_src} max clock)",
+                     "flops_per_point": flops_per_point(w.L), "migrate_ms": mig_avg},
+        "e2e": {"value": e2e_val, "unit": "point*freq/s",
+                "h2d_bytes_per_step": int(sec.nbytes + vm.nbytes), "d2h_bytes_per_step": int(d.nz * d.nx * 4),
+                "includes": "H2D section+velocity, t->f, depth loop, imaging, D2H image (table resident)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        secs, P_ref, img_ref, cores = oracle_run(w, sec, vm)
+        img_gpu = b.image.cpu().numpy()
+        # b.slab now holds the wavefield after the last e2e run (same inputs)
+        P_gpu = b.slab.cpu().numpy()
+        line["cpu_baseline"] = {"value": w.points / secs, "unit": "point*freq/s", "cores": cores,
+                                "kind": "oracle", "sample": "whole workload, FP64 depth loop (design and "
+                                "t->f excluded)", "seconds": secs}
+        line["parity"] = {"image_rel_l2": float(np.linalg.norm(img_gpu - img_ref) / np.linalg.norm(img_ref)),
+                          "final_slice_rel_l2": float(np.linalg.norm(P_gpu - P_ref) / np.linalg.norm(P_ref))}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="layered_lens_2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", type=int, default=0, help="0 auto, 1 persistent, 2 per-depth")
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--groups", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-freqs", type=int, default=24, help="frequencies per oracle step (reference arm)")
+    args = ap.parse_args(argv)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_native(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * fxmig.h -- C ABI of the GB300 library for explicit f-x poststack depth
+ * migration (libfxmig.so).
+ *
+ * Method: Shawahna, Salam, Al-Mouhamed, "Seismic Imaging: An Overview and
+ * Parallel Implementation of Poststack Depth Migration", arXiv 1912.05529.
+ *   Algorithm 1  t -> f transform of the zero-offset section, then for every
+ *                depth level and every frequency a table-driven FIR
+ *                extrapolation along x, then the depth row as the sum over
+ *                frequencies; the rows form the depth section.
+ *   Eq. 1        u(x_i, w, z_{k+1}) = sum_{n=-L}^{L} h[n] u(x_{i-n}, w, z_k).
+ *   Sec. III     the filter cutoff follows a wavenumber that depends on
+ *                frequency and velocity, so it may change at every point; the
+ *                filters are designed in advance and stored as a table.
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are raw pointers to memory the CALLER owns and keeps
+ *     alive until the enqueued work has finished.  Pointers documented as
+ *     "device" must be device-accessible on the current CUDA device.  The
+ *     library never allocates, frees or synchronises inside these calls (except
+ *     fxmig_check, which synchronises by design); all work is enqueued
+ *     asynchronously on `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream).  Every call can be captured into a CUDA graph.
+ *   - Complex numbers are interleaved (re, im) pairs of float (8 bytes,
+ *     "complex64") or double (16 bytes).
+ *   - Return value: FXMIG_OK (0) or a negative FXMIG_E* code.  Argument errors
+ *     are detected on the host before anything is enqueued.  Launch errors
+ *     return FXMIG_ECUDA (detail in fxmig_last_error()).  Conditions found by
+ *     the kernels themselves (bad velocity values, a bounded wait that gave up)
+ *     are recorded in a status word inside the caller's workspace and reported
+ *     by fxmig_check().
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef FXMIG_H
+#define FXMIG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FXMIG_VERSION 1
+
+/* Return codes. */
+#define FXMIG_OK         0
+#define FXMIG_EINVAL    -1  /* bad size, null pointer, misalignment, unsupported parameter */
+#define FXMIG_ENOSPC    -2  /* workspace or partial-image buffer too small */
+#define FXMIG_ECUDA     -3  /* a CUDA call failed; see fxmig_last_error() */
+#define FXMIG_ETIMEOUT  -4  /* (device) a bounded wait inside a kernel gave up */
+#define FXMIG_EVELOCITY -5  /* (device) a velocity sample was not finite and > 0 */
+
+/* Workspace kinds for fxmig_workspace_bytes(). */
+#define FXMIG_WS_T2F      1
+#define FXMIG_WS_MIGRATE  2
+
+/* Migration forms for fxmig_launch.mode. */
+#define FXMIG_MODE_AUTO       0
+#define FXMIG_MODE_PERSISTENT 1  /* one launch; each frequency line stays in shared memory for all depths */
+#define FXMIG_MODE_PER_DEPTH  2  /* one launch per depth step; the wavefield streams through L2/HBM */
+
+/* Problem description (all fields are read, none written).
+ *   nx      traces, x_i = i dx, i in [0, nx)                        (Eq. 1's x_i)
+ *   nz      depth rows, z_k = k dz, k in [0, nz)                    (Eq. 1's z_k)
+ *   nt      time samples of the input section, spacing dt
+ *   nw      frequency bins migrated: w_j = 2 pi (i0 + j) / (nt dt), j in [0, nw)
+ *   i0      first bin; 1 <= i0 and i0 + nw <= (nt - 1) / 2 + 1 (no DC, no Nyquist)
+ *   L       operator half-length: 2L+1 symmetric taps h[-L..L], h[-n] = h[n]
+ *   nk      wavenumber samples of the operator table, k_j = j dk, dk = k_max / (nk-1)
+ *   dx, dz, dt           sampling (m, m, s), all > 0
+ *   theta_max_deg        design dip: weight 1 for kx <= k sin(theta_max)
+ *   k_max                largest tabulated wavenumber (rad/m); normally
+ *                        w_max / min(v), with v the migration velocity */
+typedef struct fxmig_desc {
+    int nx, nz, nt, nw, i0, L, nk;
+    double dx, dz, dt, theta_max_deg, k_max;
+} fxmig_desc;
+
+/* Launch choices for fxmig_migrate_ex(); zero-initialised means "choose".
+ *   mode           FXMIG_MODE_*
+ *   cluster        CTAs sharing one frequency line along x in the persistent
+ *                  form (1, 2, 4 or 8), 0 = choose
+ *   groups         frequency groups (CTA clusters) in the persistent form, or
+ *                  frequency tiles in the per-depth form; 0 = choose
+ *   warps          warps per CTA (persistent form), 0 = choose */
+typedef struct fxmig_launch {
+    int mode, cluster, groups, warps;
+} fxmig_launch;
+
+/* Library version (FXMIG_VERSION of the build). */
+int fxmig_version(void);
+
+/* Text for a return code; never NULL. */
+const char *fxmig_strerror(int code);
+
+/* Detail of the last FXMIG_ECUDA returned on this host thread ("" if none). */
+const char *fxmig_last_error(void);
+
+/* Bytes of device workspace that `kind` (FXMIG_WS_*) needs for `d`; 0 if d is
+ * invalid.  The workspace is caller-owned scratch, must be 256-byte aligned,
+ * and must not be shared by calls that may run concurrently. */
+size_t fxmig_workspace_bytes(const fxmig_desc *d, int kind);
+
+/* Number of partial images fxmig_migrate_ex() writes for `d` and `launch`
+ * (NULL = automatic choices); the partials buffer holds that many [nz][nx]
+ * float images.  Returns a negative code if d is invalid. */
+int fxmig_num_partials(const fxmig_desc *d, const fxmig_launch *launch);
+
+/* Operator table design (Sec. II: the filter design is an optimisation
+ * between short and long filters; Sec. III: filters designed in advance and
+ * stored).  For every k_j = j dk the symmetric taps h[0..L] minimise
+ *   sum_m w_m |H(kx_m) - D(kx_m)|^2,  H(kx) = h0 + 2 sum_{n>=1} h_n cos(n kx dx),
+ * on M = max(256, 16(L+1)) samples kx_m = m pi / (dx (M-1)), against the
+ * one-way phase shift D = exp(+i sqrt(k^2 - kx^2) dz) (kx <= k) and
+ * D = exp(-sqrt(kx^2 - k^2) dz) (kx > k), with w = 1 for kx <= k sin(theta_max)
+ * and 1e-2 elsewhere; solved in FP64 on the device (normal equations,
+ * Cholesky).  Then the amplitude guard: with G = max |H| over 4096 samples of
+ * [0, pi/dx], taps are scaled by 1/G when G > 1 (|H| <= 1 keeps the recursion
+ * of Eq. 1 stable, Sec. II).
+ *   table     device, out: [nk][L+1] complex64
+ *   table64   device, out, may be NULL: [nk][L+1] complex double (FP64 taps)
+ * Errors: FXMIG_EINVAL for an invalid d or a NULL table. */
+int fxmig_design_operators(const fxmig_desc *d, void *table, void *table64, void *stream);
+
+/* Time -> frequency transform of the zero-offset section (Algorithm 1, "Fourier
+ * transform along the t-axis"; Sec. III): a batched mixed-radix real FFT of
+ * every trace, keeping the band bins only:
+ *   slab[j][x] = sum_{t=0}^{nt-1} section[x][t] exp(-2 pi i (i0+j) t / nt)
+ * (forward sign, no scaling).
+ *   section   device, in:  [nx][nt] float, trace-major
+ *   slab      device, out: [nw][nx] complex64 (frequency-major)
+ *   ws        device scratch of fxmig_workspace_bytes(d, FXMIG_WS_T2F) bytes
+ * Errors: FXMIG_EINVAL (invalid d, NULL pointer, nt with a prime factor above 13),
+ * FXMIG_ENOSPC (ws_bytes too small). */
+int fxmig_t2f(const fxmig_desc *d, const float *section, void *slab,
+              void *ws, size_t ws_bytes, void *stream);
+
+/* Depth loop of Algorithm 1 over rows [z_begin, z_end), 0 <= z_begin <= z_end <= nz:
+ *   for z: image row z = sum_j Re slab[j][x]       (taken before the step; row 0
+ *                                                     is the surface)
+ *          slab[j][x] <- sum_{n=-L}^{L} h_{j,x,z}[|n|] slab[j][x-n]     (Eq. 1)
+ * with slab = 0 outside [0, nx) and taps h_{j,x,z} = table[idx], where
+ *   idx = min(nk-1, max(0, rint_half_even(fl32(q_j * s))))
+ *   q_j = fl32(w_j / dk) (computed in FP64, rounded once), s = fl32(1 / vel[z][x])
+ * (Sec. III: per-point choice of the filter by wavenumber; nearest entry).
+ *   slab      device, in/out: [nw][nx] complex64; in: wavefield at depth z_begin,
+ *             out: wavefield at depth z_end.  Splitting [0, nz) into consecutive
+ *             calls gives the same result as one call (checkpoint / resume).
+ *   vel       device, in: [nz][nx] float migration velocity (m/s), finite and > 0
+ *             (exploding-reflector data: half the medium velocity)
+ *   table     device, in: [nk][L+1] complex64, as written by fxmig_design_operators
+ *   partials  device, out: [nparts][nz][nx] float, nparts = fxmig_num_partials(d, launch);
+ *             rows [z_begin, z_end) of every partial are written, other rows are
+ *             left untouched.  The image is their sum (fxmig_image).
+ *   ws        device scratch of fxmig_workspace_bytes(d, FXMIG_WS_MIGRATE) bytes;
+ *             its status word is cleared at the start of every call.
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC (nparts or ws_bytes too small), FXMIG_ECUDA;
+ * device-side FXMIG_EVELOCITY / FXMIG_ETIMEOUT via fxmig_check(ws). */
+int fxmig_migrate(const fxmig_desc *d, void *slab, const float *vel, const void *table,
+                  float *partials, int nparts, int z_begin, int z_end,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* fxmig_migrate with explicit launch choices (NULL = automatic). */
+int fxmig_migrate_ex(const fxmig_desc *d, const fxmig_launch *launch, void *slab,
+                     const float *vel, const void *table, float *partials, int nparts,
+                     int z_begin, int z_end, void *ws, size_t ws_bytes, void *stream);
+
+/* Imaging (Algorithm 1, "calculate depth row by summing over frequencies";
+ * Sec. III, second kernel): image[z][x] = sum_{p=0}^{nparts-1} partials[p][z][x],
+ * summed in ascending p, so the result is deterministic.
+ *   partials  device, in: [nparts][nz][nx] float
+ *   image     device, out: [nz][nx] float
+ * Errors: FXMIG_EINVAL. */
+int fxmig_image(const fxmig_desc *d, const float *partials, int nparts, float *image, void *stream);
+
+/* Waits for `stream`, then reads and returns the device status word in `ws`
+ * (FXMIG_OK, FXMIG_EVELOCITY or FXMIG_ETIMEOUT); FXMIG_ECUDA if the stream
+ * reports a CUDA error; FXMIG_EINVAL for a NULL ws. */
+int fxmig_check(const void *ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FXMIG_H */

@@ -1,0 +1,269 @@
+"""GB300 (sm_103a) library for explicit f-x poststack depth migration.
+
+Thin ctypes binding over the C ABI of ``libfxmig.so`` (``include/fxmig.h``):
+the functions below carry the C names, check and marshal their arguments
+(torch tensors -> raw device pointers, the current torch stream -> cudaStream_t)
+and raise ``FxmigError`` on a non-zero return code.  Every step of the method
+runs in the library's CUDA kernels; PyTorch only provides device memory and
+streams.  There is no CPU fallback: if the library is missing this module
+raises on import of any entry point.
+
+Method: Shawahna, Salam, Al-Mouhamed, "Seismic Imaging: An Overview and Parallel
+Implementation of Poststack Depth Migration", arXiv 1912.05529 (Algorithm 1,
+Eq. 1, Sec. III).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+__all__ = [
+    "FXMIG_OK", "FXMIG_EINVAL", "FXMIG_ENOSPC", "FXMIG_ECUDA", "FXMIG_ETIMEOUT", "FXMIG_EVELOCITY",
+    "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
+    "FxmigError", "Desc", "Launch", "lib", "library_path",
+    "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
+    "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
+    "fxmig_check", "desc_for", "migrate_section",
+]
+
+FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
+FXMIG_WS_T2F, FXMIG_WS_MIGRATE = 1, 2
+FXMIG_MODE_AUTO, FXMIG_MODE_PERSISTENT, FXMIG_MODE_PER_DEPTH = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libfxmig.so")
+_lib = None
+
+
+class FxmigError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        detail = ""
+        if code == FXMIG_ECUDA and _lib is not None:
+            detail = ": " + _lib.fxmig_last_error().decode()
+        super().__init__(f"{where} failed: {fxmig_strerror(code)} ({code}){detail}")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    """Mirror of ``fxmig_desc``."""
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int), ("nw", ctypes.c_int),
+                ("i0", ctypes.c_int), ("L", ctypes.c_int), ("nk", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+                ("theta_max_deg", ctypes.c_double), ("k_max", ctypes.c_double)]
+
+    def __repr__(self):
+        return "Desc(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
+
+
+class Launch(ctypes.Structure):
+    """Mirror of ``fxmig_launch`` (zeros = automatic)."""
+    _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
+                ("warps", ctypes.c_int)]
+
+
+def lib():
+    """Load libfxmig.so (built by ``paper_1912_05529_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"{library_path} is missing: build it with "
+                              "`python -m paper_1912_05529_gb300.build` (nvcc, sm_103a)")
+        L = ctypes.CDLL(library_path)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        pd, pl = ctypes.POINTER(Desc), ctypes.POINTER(Launch)
+        L.fxmig_version.restype = i
+        L.fxmig_strerror.argtypes = [i]
+        L.fxmig_strerror.restype = ctypes.c_char_p
+        L.fxmig_last_error.restype = ctypes.c_char_p
+        L.fxmig_workspace_bytes.argtypes = [pd, i]
+        L.fxmig_workspace_bytes.restype = sz
+        L.fxmig_num_partials.argtypes = [pd, pl]
+        L.fxmig_num_partials.restype = i
+        L.fxmig_design_operators.argtypes = [pd, vp, vp, vp]
+        L.fxmig_t2f.argtypes = [pd, vp, vp, vp, sz, vp]
+        L.fxmig_migrate.argtypes = [pd, vp, vp, vp, vp, i, i, i, vp, sz, vp]
+        L.fxmig_migrate_ex.argtypes = [pd, pl, vp, vp, vp, vp, i, i, i, vp, sz, vp]
+        L.fxmig_image.argtypes = [pd, vp, i, vp, vp]
+        L.fxmig_check.argtypes = [vp, vp]
+        for f in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex",
+                  "fxmig_image", "fxmig_check"):
+            getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, what, dtype=None, numel=None, complex_ok=False):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    if dtype is not None:
+        ok = t.dtype == dtype or (complex_ok and t.dtype == torch.complex64 and dtype == torch.float32)
+        if not ok:
+            raise TypeError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if numel is not None:
+        n = t.numel() * (2 if t.is_complex() else 1)
+        if n < numel:
+            raise ValueError(f"{what}: {n} elements, need {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code, where):
+    if code != FXMIG_OK:
+        raise FxmigError(code, where)
+
+
+# ---------------------------------------------------------------- C entry points
+def fxmig_version() -> int:
+    return lib().fxmig_version()
+
+
+def fxmig_strerror(code: int) -> str:
+    return lib().fxmig_strerror(code).decode()
+
+
+def fxmig_workspace_bytes(d: Desc, kind: int) -> int:
+    return int(lib().fxmig_workspace_bytes(ctypes.byref(d), kind))
+
+
+def fxmig_num_partials(d: Desc, launch: Launch | None = None) -> int:
+    n = lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(launch) if launch else None)
+    if n < 0:
+        raise FxmigError(n, "fxmig_num_partials")
+    return n
+
+
+def fxmig_design_operators(d: Desc, table, table64=None, stream=None) -> None:
+    """table: [nk][L+1] complex64 (device); table64: [nk][L+1] complex128 or None."""
+    torch = _torch()
+    n = d.nk * (d.L + 1)
+    tp = _dev_ptr(table, "table", torch.float32, 2 * n, complex_ok=True)
+    t64 = None
+    if table64 is not None:
+        if table64.dtype not in (torch.complex128, torch.float64):
+            raise TypeError("table64: expected complex128 or float64")
+        t64 = _dev_ptr(table64, "table64", None, 2 * n)
+    _check(lib().fxmig_design_operators(ctypes.byref(d), tp, t64, _stream(stream)), "fxmig_design_operators")
+
+
+def fxmig_t2f(d: Desc, section, slab, ws, stream=None) -> None:
+    """section: [nx][nt] float32; slab: [nw][nx] complex64; ws: uint8 scratch."""
+    torch = _torch()
+    sp = _dev_ptr(section, "section", torch.float32, d.nx * d.nt)
+    bp = _dev_ptr(slab, "slab", torch.float32, 2 * d.nw * d.nx, complex_ok=True)
+    wp = _dev_ptr(ws, "ws")
+    _check(lib().fxmig_t2f(ctypes.byref(d), sp, bp, wp, ws.numel() * ws.element_size(), _stream(stream)),
+           "fxmig_t2f")
+
+
+def fxmig_migrate_ex(d: Desc, launch: Launch | None, slab, vel, table, partials, z_begin, z_end, ws,
+                     stream=None) -> None:
+    torch = _torch()
+    bp = _dev_ptr(slab, "slab", torch.float32, 2 * d.nw * d.nx, complex_ok=True)
+    vp = _dev_ptr(vel, "vel", torch.float32, d.nz * d.nx)
+    tp = _dev_ptr(table, "table", torch.float32, 2 * d.nk * (d.L + 1), complex_ok=True)
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * d.nx)
+    wp = _dev_ptr(ws, "ws")
+    rc = lib().fxmig_migrate_ex(ctypes.byref(d), ctypes.byref(launch) if launch else None, bp, vp, tp, pp,
+                                int(nparts), int(z_begin), int(z_end), wp, ws.numel() * ws.element_size(),
+                                _stream(stream))
+    _check(rc, "fxmig_migrate")
+
+
+def fxmig_migrate(d: Desc, slab, vel, table, partials, z_begin, z_end, ws, stream=None) -> None:
+    """slab: [nw][nx] complex64 in/out; vel: [nz][nx] float32; table: [nk][L+1]
+    complex64; partials: [nparts][nz][nx] float32; ws: uint8 scratch."""
+    fxmig_migrate_ex(d, None, slab, vel, table, partials, z_begin, z_end, ws, stream)
+
+
+def fxmig_image(d: Desc, partials, image, stream=None) -> None:
+    torch = _torch()
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * d.nx)
+    ip = _dev_ptr(image, "image", torch.float32, d.nz * d.nx)
+    _check(lib().fxmig_image(ctypes.byref(d), pp, int(nparts), ip, _stream(stream)), "fxmig_image")
+
+
+def fxmig_check(ws, stream=None) -> int:
+    """Synchronise the stream and return the device status code (0 = ok)."""
+    return int(lib().fxmig_check(_dev_ptr(ws, "ws"), _stream(stream)))
+
+
+# ------------------------------------------------------------------ conveniences
+def desc_for(nx, nz, nt, dx, dz, dt, f_lo, f_hi, L, v_min, nk=1024, theta_deg=65.0) -> Desc:
+    """Descriptor of a problem: band bins f_lo <= j/(nt dt) <= f_hi and a table
+    spanning k up to w_max / v_min (v_min: smallest migration velocity)."""
+    df = 1.0 / (nt * dt)
+    i0 = max(1, int(math.ceil(f_lo / df - 1e-9)))
+    i1 = min((nt - 1) // 2, int(math.floor(f_hi / df + 1e-9)))
+    nw = i1 - i0 + 1
+    k_max = 2.0 * math.pi * (i0 + nw - 1) / (nt * dt) / v_min
+    return Desc(nx=nx, nz=nz, nt=nt, nw=nw, i0=i0, L=L, nk=nk, dx=dx, dz=dz, dt=dt,
+                theta_max_deg=theta_deg, k_max=k_max)
+
+
+@dataclasses.dataclass
+class Buffers:
+    """Device buffers of one migration (caller-owned, reusable across calls)."""
+    section: object
+    slab: object
+    vel: object
+    table: object
+    partials: object
+    image: object
+    ws_t2f: object
+    ws_mig: object
+
+
+def allocate(d: Desc, launch: Launch | None = None, device="cuda") -> Buffers:
+    torch = _torch()
+    nparts = fxmig_num_partials(d, launch)
+    return Buffers(
+        section=torch.empty((d.nx, d.nt), dtype=torch.float32, device=device),
+        slab=torch.empty((d.nw, d.nx), dtype=torch.complex64, device=device),
+        vel=torch.empty((d.nz, d.nx), dtype=torch.float32, device=device),
+        table=torch.empty((d.nk, d.L + 1), dtype=torch.complex64, device=device),
+        partials=torch.empty((nparts, d.nz, d.nx), dtype=torch.float32, device=device),
+        image=torch.empty((d.nz, d.nx), dtype=torch.float32, device=device),
+        ws_t2f=torch.empty(fxmig_workspace_bytes(d, FXMIG_WS_T2F), dtype=torch.uint8, device=device),
+        ws_mig=torch.empty(fxmig_workspace_bytes(d, FXMIG_WS_MIGRATE), dtype=torch.uint8, device=device),
+    )
+
+
+def migrate_section(d: Desc, section_host, vel_host, bufs: Buffers | None = None, launch: Launch | None = None,
+                    image_host=None, design: bool = True, stream=None):
+    """End-to-end migration from host arrays (Algorithm 1): copy the section and
+    velocity to the device, t -> f, (design the table), depth loop, imaging,
+    copy the image back.  Returns the host image tensor [nz][nx]."""
+    torch = _torch()
+    b = bufs or allocate(d, launch)
+    b.section.copy_(section_host, non_blocking=True)
+    b.vel.copy_(vel_host, non_blocking=True)
+    if design:
+        fxmig_design_operators(d, b.table, None, stream)
+    fxmig_t2f(d, b.section, b.slab, b.ws_t2f, stream)
+    fxmig_migrate_ex(d, launch, b.slab, b.vel, b.table, b.partials, 0, d.nz, b.ws_mig, stream)
+    fxmig_image(d, b.partials, b.image, stream)
+    if image_host is None:
+        image_host = torch.empty((d.nz, d.nx), dtype=torch.float32, pin_memory=True)
+    image_host.copy_(b.image, non_blocking=True)
+    return image_host

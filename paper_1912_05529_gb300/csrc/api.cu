@@ -1,0 +1,132 @@
+// api.cu -- the C ABI of libfxmig (include/fxmig.h): argument checks on the
+// host, then asynchronous launches on the caller's stream.  No allocation, no
+// synchronisation (fxmig_check excepted), no exception crosses the boundary.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "fxmig_internal.cuh"
+
+using namespace fxmig_impl;
+
+namespace fxmig_impl {
+
+bool desc_valid(const fxmig_desc* d) {
+    if (!d) return false;
+    if (d->nx < 1 || d->nz < 1 || d->nt < 2 || d->nw < 1 || d->L < 0 || d->nk < 1) return false;
+    if (d->i0 < 1 || (long long)d->i0 + d->nw > (long long)((d->nt - 1) / 2) + 1) return false;
+    if (!(d->dx > 0) || !(d->dz >= 0) || !(d->dt > 0) || !isfinite(d->dx) || !isfinite(d->dz) || !isfinite(d->dt))
+        return false;
+    if (!(d->theta_max_deg >= 0 && d->theta_max_deg <= 90)) return false;
+    if (!(d->k_max >= 0) || !isfinite(d->k_max)) return false;
+    if (d->nk > 1 && !(d->k_max > 0)) return false;
+    if (compiled_half_length(d->L) < 0) return false;
+    // sizes that must fit 32-bit indexing of one line / one image plane
+    if ((long long)d->nx * d->nz > (1LL << 31) || (long long)d->nx * d->nw > (1LL << 31)) return false;
+    return true;
+}
+
+}  // namespace fxmig_impl
+
+static thread_local char g_last_error[256] = "";
+
+static int cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    return FXMIG_ECUDA;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+extern "C" {
+
+int fxmig_version(void) { return FXMIG_VERSION; }
+
+const char* fxmig_strerror(int code) {
+    switch (code) {
+        case FXMIG_OK: return "ok";
+        case FXMIG_EINVAL: return "invalid argument";
+        case FXMIG_ENOSPC: return "workspace or partial-image buffer too small";
+        case FXMIG_ECUDA: return "CUDA error";
+        case FXMIG_ETIMEOUT: return "a bounded wait on the device gave up";
+        case FXMIG_EVELOCITY: return "velocity sample not finite and positive";
+        default: return "unknown error";
+    }
+}
+
+const char* fxmig_last_error(void) { return g_last_error; }
+
+size_t fxmig_workspace_bytes(const fxmig_desc* d, int kind) {
+    if (!desc_valid(d)) return 0;
+    if (kind == FXMIG_WS_T2F) return t2f_ws_bytes(d);
+    if (kind == FXMIG_WS_MIGRATE) return migrate_ws_bytes(d);
+    return 0;
+}
+
+int fxmig_num_partials(const fxmig_desc* d, const fxmig_launch* launch) {
+    if (!desc_valid(d)) return FXMIG_EINVAL;
+    MigratePlan p;
+    const int rc = plan_migrate(d, launch, &p);
+    return rc == FXMIG_OK ? p.nparts : rc;
+}
+
+int fxmig_design_operators(const fxmig_desc* d, void* table, void* table64, void* stream) {
+    if (!desc_valid(d) || !table || !aligned(table, 8) || (table64 && !aligned(table64, 16))) return FXMIG_EINVAL;
+    const cudaError_t e = launch_design(d, table, table64, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_design_operators");
+}
+
+int fxmig_t2f(const fxmig_desc* d, const float* section, void* slab, void* ws, size_t ws_bytes, void* stream) {
+    if (!desc_valid(d) || !section || !slab || !ws) return FXMIG_EINVAL;
+    if (!aligned(section, 4) || !aligned(slab, 8) || !aligned(ws, 256)) return FXMIG_EINVAL;
+    if (!t2f_supported(d->nt)) return FXMIG_EINVAL;
+    if (ws_bytes < t2f_ws_bytes(d)) return FXMIG_ENOSPC;
+    const cudaError_t e = launch_t2f(d, section, slab, ws, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_t2f");
+}
+
+int fxmig_migrate_ex(const fxmig_desc* d, const fxmig_launch* launch, void* slab, const float* vel,
+                     const void* table, float* partials, int nparts, int z_begin, int z_end, void* ws,
+                     size_t ws_bytes, void* stream) {
+    if (!desc_valid(d) || !slab || !vel || !table || !partials || !ws) return FXMIG_EINVAL;
+    if (!aligned(slab, 8) || !aligned(vel, 4) || !aligned(table, 8) || !aligned(partials, 16) || !aligned(ws, 256))
+        return FXMIG_EINVAL;
+    if (z_begin < 0 || z_end < z_begin || z_end > d->nz) return FXMIG_EINVAL;
+    MigratePlan plan;
+    const int rc = plan_migrate(d, launch, &plan);
+    if (rc != FXMIG_OK) return rc;
+    if (nparts < plan.nparts || ws_bytes < migrate_ws_bytes(d)) return FXMIG_ENOSPC;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (z_begin == z_end) {
+        const cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), s);
+        return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate");
+    }
+    const cudaError_t e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s);
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate");
+}
+
+int fxmig_migrate(const fxmig_desc* d, void* slab, const float* vel, const void* table, float* partials,
+                  int nparts, int z_begin, int z_end, void* ws, size_t ws_bytes, void* stream) {
+    return fxmig_migrate_ex(d, nullptr, slab, vel, table, partials, nparts, z_begin, z_end, ws, ws_bytes, stream);
+}
+
+int fxmig_image(const fxmig_desc* d, const float* partials, int nparts, float* image, void* stream) {
+    if (!desc_valid(d) || !partials || !image || nparts < 0) return FXMIG_EINVAL;
+    if (!aligned(partials, 4) || !aligned(image, 4)) return FXMIG_EINVAL;
+    const cudaError_t e = launch_image(d, partials, nparts, image, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_image");
+}
+
+int fxmig_check(const void* ws, void* stream) {
+    if (!ws) return FXMIG_EINVAL;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "fxmig_check");
+    int status = 0;
+    e = cudaMemcpy(&status, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fxmig_check");
+    if (status & kStatusTimeout) return FXMIG_ETIMEOUT;
+    if (status & kStatusVelocity) return FXMIG_EVELOCITY;
+    return FXMIG_OK;
+}
+
+}  // extern "C"

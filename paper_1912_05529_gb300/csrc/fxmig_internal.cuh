@@ -1,0 +1,154 @@
+// fxmig_internal.cuh -- device helpers and internal host interfaces shared by
+// the CUDA translation units of libfxmig (sm_103a only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fxmig.h"
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ < 1000)
+#error "libfxmig targets Blackwell (sm_103a)"
+#endif
+
+namespace fxmig_impl {
+
+// ----------------------------------------------------------------- status word
+// Bits OR-ed into the workspace status word by kernels; fxmig_check maps them
+// to return codes.
+enum : int {
+    kStatusTimeout = 1,   // a bounded mbarrier wait gave up
+    kStatusVelocity = 2,  // a velocity sample was not finite and > 0
+};
+constexpr size_t kStatusBytes = 256;  // status word + padding at the workspace start
+
+// Largest operator half-length compiled into the extrapolation kernels; other
+// L are rounded up to the next compiled length with zero taps.
+constexpr int kMaxL = 32;
+int compiled_half_length(int L);  // smallest compiled LT >= L, or -1
+
+// ------------------------------------------------------------ packed FP32 ops
+// Blackwell executes two FP32 operations per lane with one f32x2 instruction.
+// A u64 register holds (lo, hi) = (re, im) of a complex64 value.
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 f2_pack(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(u64 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ u64 f2_add(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_mul(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 f2_fma(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 16-byte read-only global load returning two packed pairs.
+__device__ __forceinline__ void ldg_nc_v2(const void* p, u64& a, u64& b) {
+    asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+
+// ------------------------------------------------------------ mbarrier + bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> own shared memory, completion counted on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for phase `parity` of `bar`.  Returns false (and leaves the
+// caller to record a timeout) after `max_iter` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr uint32_t kWaitPolls = 1u << 22;  // try_wait suspends between polls: seconds in total
+
+// ------------------------------------------------------------------- clusters
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory variable in CTA `rank` of this cluster,
+// as a shared::cluster address usable with st.shared::cluster.
+__device__ __forceinline__ uint32_t map_cluster_rank(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// ------------------------------------------------------------ host interfaces
+struct MigratePlan {
+    int mode;      // FXMIG_MODE_PERSISTENT or FXMIG_MODE_PER_DEPTH
+    int LT;        // compiled half-length >= L
+    int cluster;   // persistent: CTAs per frequency group along x
+    int groups;    // persistent: frequency groups; per-depth: frequency tiles
+    int warps;     // warps per CTA
+    int W;         // persistent: x segment per CTA (multiple of 8)
+    int lines;     // persistent: max lines per group
+    size_t smem;   // dynamic shared memory bytes per CTA
+    int nparts;    // partial images written
+};
+
+bool desc_valid(const fxmig_desc* d);
+int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* plan);
+size_t migrate_ws_bytes(const fxmig_desc* d);
+size_t t2f_ws_bytes(const fxmig_desc* d);
+bool t2f_supported(int nt);
+
+cudaError_t launch_design(const fxmig_desc* d, void* table, void* table64, cudaStream_t s);
+cudaError_t launch_t2f(const fxmig_desc* d, const float* section, void* slab, void* ws, cudaStream_t s);
+cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* vel,
+                           const void* table, float* partials, int z_begin, int z_end, void* ws,
+                           cudaStream_t s);
+cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
+                         cudaStream_t s);
+
+}  // namespace fxmig_impl

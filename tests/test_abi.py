@@ -1,0 +1,119 @@
+"""The C ABI library builds for sm_103a, loads, exports every entry point that
+include/fxmig.h declares, and rejects bad arguments on the host (no GPU needed:
+none of these calls reaches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fx():
+    from paper_1912_05529_gb300 import build
+    build.build()
+    import paper_1912_05529_gb300 as fx
+    fx.lib()
+    return fx
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fxmig.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\s*\*)\s*\*?\s*(fxmig_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_image"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(fx):
+    lib = fx.lib()
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_version_and_strerror(fx):
+    assert fx.fxmig_version() == 1
+    for code in (0, -1, -2, -3, -4, -5):
+        assert fx.fxmig_strerror(code) and fx.fxmig_strerror(code) != "unknown error"
+    assert fx.fxmig_strerror(-99) == "unknown error"
+
+
+def _desc(fx, **kw):
+    d = fx.desc_for(nx=128, nz=100, nt=256, dx=10.0, dz=5.0, dt=0.004, f_lo=5.0, f_hi=60.0, L=12, v_min=1000.0)
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_descriptor_band(fx):
+    d = _desc(fx)
+    assert (d.i0, d.nw) == (6, 56)
+
+
+def test_workspace_sizes(fx):
+    d = _desc(fx)
+    assert fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_T2F) >= 256 + 8 * d.nt
+    assert fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MIGRATE) >= 256 + 16 * d.nk * (d.L + 1)
+    assert fx.fxmig_workspace_bytes(d, 99) == 0
+    assert fx.fxmig_workspace_bytes(_desc(fx, nx=0), fx.FXMIG_WS_T2F) == 0
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=0), dict(nw=0), dict(i0=0), dict(i0=120),
+                                 dict(L=21), dict(dx=0.0), dict(dt=-1.0), dict(k_max=float("nan")),
+                                 dict(theta_max_deg=120.0)])
+def test_invalid_descriptors_are_rejected(fx, bad):
+    d = _desc(fx, **bad)
+    lib = fx.lib()
+    dummy = ctypes.c_void_p(256)
+    assert lib.fxmig_design_operators(ctypes.byref(d), dummy, None, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_t2f(ctypes.byref(d), dummy, dummy, dummy, 1 << 20, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_migrate(ctypes.byref(d), dummy, dummy, dummy, dummy, 1, 0, 1, dummy, 1 << 30, None) \
+        == fx.FXMIG_EINVAL
+    assert lib.fxmig_image(ctypes.byref(d), dummy, 1, dummy, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_num_partials(ctypes.byref(d), None) == fx.FXMIG_EINVAL
+
+
+def test_null_and_misaligned_pointers(fx):
+    d = _desc(fx)
+    lib = fx.lib()
+    ok = ctypes.c_void_p(1 << 20)
+    big = 1 << 30
+    assert lib.fxmig_design_operators(ctypes.byref(d), None, None, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_t2f(ctypes.byref(d), None, ok, ok, big, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_t2f(ctypes.byref(d), ok, ok, ctypes.c_void_p((1 << 20) + 8), big, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_migrate(ctypes.byref(d), ok, None, ok, ok, 1000, 0, 1, ok, big, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_migrate(ctypes.byref(d), ok, ok, ok, ctypes.c_void_p((1 << 20) + 4), 1000, 0, 1, ok, big,
+                             None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_image(ctypes.byref(d), None, 1, ok, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_check(None, None) == fx.FXMIG_EINVAL
+
+
+def test_bad_depth_range_and_small_buffers(fx):
+    d = _desc(fx)
+    lib = fx.lib()
+    ok = ctypes.c_void_p(1 << 20)
+    big = 1 << 30
+    for zb, ze in ((-1, 5), (5, 4), (0, 101)):
+        assert lib.fxmig_migrate(ctypes.byref(d), ok, ok, ok, ok, 1000, zb, ze, ok, big, None) == fx.FXMIG_EINVAL
+    need = fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MIGRATE)
+    assert lib.fxmig_migrate(ctypes.byref(d), ok, ok, ok, ok, 1000, 0, 5, ok, need - 1, None) == fx.FXMIG_ENOSPC
+    assert lib.fxmig_migrate(ctypes.byref(d), ok, ok, ok, ok, 0, 0, 5, ok, need, None) == fx.FXMIG_ENOSPC
+    assert lib.fxmig_t2f(ctypes.byref(d), ok, ok, ok, 16, None) == fx.FXMIG_ENOSPC
+
+
+def test_unsupported_fft_length(fx):
+    d = _desc(fx, nt=2 * 17 * 19, i0=3, nw=10)
+    lib = fx.lib()
+    ok = ctypes.c_void_p(1 << 20)
+    assert lib.fxmig_t2f(ctypes.byref(d), ok, ok, ok, 1 << 30, None) == fx.FXMIG_EINVAL
+
+
+def test_invalid_launch_choices(fx):
+    d = _desc(fx)
+    assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(mode=7))) == fx.FXMIG_EINVAL
+    assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(cluster=3))) == fx.FXMIG_EINVAL

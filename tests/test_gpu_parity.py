@@ -1,0 +1,160 @@
+"""GPU parity of every hot-path kernel against the FP64 oracle, through the C ABI.
+
+Each kernel gets the oracle's own inputs (rounded to the fp32 the kernel
+takes), so only the kernel's arithmetic is under test; the end-to-end test then
+runs every GPU step from the raw section."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from fxhelp import (TOL_DESIGN64, TOL_IMAGE, TOL_SLICE, TOL_T2F, desc_of, layered_inputs, problem, rel_l2,
+                    small_layered)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_05529_gb300 import build
+    build.build()
+    import paper_1912_05529_gb300 as fx
+    return fx
+
+
+def _cuda(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def run_gpu_migrate(fx, d, P0_32, vm, table32, launch=None, chunks=None):
+    """Returns (slabs after each chunk, image) from the library."""
+    slab = _cuda(P0_32, torch.complex64)
+    vel = _cuda(vm, torch.float32)
+    table = _cuda(table32, torch.complex64)
+    nparts = fx.fxmig_num_partials(d, launch)
+    partials = torch.full((nparts, d.nz, d.nx), float("nan"), dtype=torch.float32, device="cuda")
+    ws = torch.zeros(fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MIGRATE), dtype=torch.uint8, device="cuda")
+    image = torch.empty((d.nz, d.nx), dtype=torch.float32, device="cuda")
+    bounds = chunks or [0, d.nz]
+    slabs = []
+    for zb, ze in zip(bounds[:-1], bounds[1:]):
+        fx.fxmig_migrate_ex(d, launch, slab, vel, table, partials, zb, ze, ws)
+        slabs.append(slab.cpu().numpy().copy())
+    assert fx.fxmig_check(ws) == fx.FXMIG_OK
+    fx.fxmig_image(d, partials, image)
+    torch.cuda.synchronize()
+    return slabs, image.cpu().numpy()
+
+
+def test_design_matches_oracle(fx):
+    for (dx, dz, L, kmax) in [(10.0, 5.0, 12, 2 * math.pi * 59.57 / 1000), (12.5, 5.0, 12, 0.503),
+                              (6.25, 4.0, 17, 0.67), (12.5, 5.0, 8, 0.3), (12.5, 0.0, 4, 0.3)]:
+        d = fx.Desc(nx=8, nz=1, nt=64, nw=1, i0=1, L=L, nk=1024, dx=dx, dz=dz, dt=0.004, theta_max_deg=65.0,
+                    k_max=kmax)
+        t32 = torch.empty((1024, L + 1), dtype=torch.complex64, device="cuda")
+        t64 = torch.empty((1024, L + 1), dtype=torch.complex128, device="cuda")
+        fx.fxmig_design_operators(d, t32, t64)
+        ref = O.design_operators(1024, kmax, dx, dz, L, 65.0)
+        g64 = t64.cpu().numpy()
+        err = np.max(np.abs(g64 - ref)) / np.max(np.abs(ref))
+        assert err < TOL_DESIGN64, (dx, dz, L, err)
+        g32 = t32.cpu().numpy()
+        assert np.max(np.abs(g32 - ref.astype(np.complex64))) <= 2 * 2 ** -24 * np.max(np.abs(ref)) + 1e-30
+
+
+@pytest.mark.parametrize("nx,nt,i0,nw", [(128, 256, 6, 56), (37, 2000, 20, 221), (64, 4000, 40, 601),
+                                         (5, 250, 1, 124), (33, 60, 2, 20), (16, 7 * 13 * 4, 3, 100)])
+def test_t2f_matches_oracle_dft(fx, nx, nt, i0, nw):
+    rng = np.random.default_rng(nt + nx)
+    sec = rng.standard_normal((nx, nt)).astype(np.float32)
+    d = fx.Desc(nx=nx, nz=1, nt=nt, nw=nw, i0=i0, L=4, nk=2, dx=10.0, dz=5.0, dt=0.004, theta_max_deg=65.0,
+                k_max=0.1)
+    slab = torch.empty((nw, nx), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_T2F), dtype=torch.uint8, device="cuda")
+    fx.fxmig_t2f(d, _cuda(sec, torch.float32), slab, ws)
+    ref = O.band_dft(sec.astype(np.float64), i0, nw)
+    assert rel_l2(slab.cpu().numpy(), ref) < TOL_T2F * math.log2(nt)
+
+
+LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=4),
+            dict(mode=1, cluster=2, groups=7, warps=5), dict(mode=1, cluster=1, groups=200),
+            dict(mode=2), dict(mode=2, groups=3)]
+
+
+@pytest.fixture(scope="module")
+def layered_case():
+    w = small_layered()
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    chunks = [0, 1, 37, 80, w.nz]
+    slabs, image = [], np.zeros((w.nz, w.nx))
+    P = P0_32.astype(np.complex128)
+    for zb, ze in zip(chunks[:-1], chunks[1:]):
+        P, img = O.migrate(P, pr["vm"], table32.astype(np.complex128), pr["q"], zb, ze)
+        slabs.append(P.copy())
+        image[zb:ze] = img[zb:ze]
+    return w, pr, table32, P0_32, chunks, slabs, image
+
+
+@pytest.mark.parametrize("launch", LAUNCHES)
+def test_migrate_matches_oracle_per_depth_slice(fx, layered_case, launch):
+    w, pr, table32, P0_32, chunks, ref_slabs, ref_image = layered_case
+    d = desc_of(fx, w, pr["k_max"])
+    lc = fx.Launch(**launch) if launch else None
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, lc, chunks)
+    for s, r in zip(slabs, ref_slabs):
+        assert rel_l2(s, r) < TOL_SLICE
+    assert rel_l2(image, ref_image) < TOL_IMAGE
+    assert np.all(np.isfinite(image))
+
+
+def test_split_equals_unsplit_and_deterministic(fx, layered_case):
+    w, pr, table32, P0_32, chunks, _, _ = layered_case
+    d = desc_of(fx, w, pr["k_max"])
+    a_slabs, a_img = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, None, chunks)
+    b_slabs, b_img = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, None, None)
+    c_slabs, c_img = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, None, None)
+    assert np.array_equal(a_slabs[-1], b_slabs[-1]) and np.array_equal(a_img, b_img)
+    assert np.array_equal(b_slabs[-1], c_slabs[-1]) and np.array_equal(b_img, c_img)
+
+
+@pytest.mark.parametrize("L", [4, 8, 17, 20])
+def test_other_filter_lengths(fx, L):
+    w = small_layered(nx=300, nz=40, L=L, seed=9)
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    P, img = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    d = desc_of(fx, w, pr["k_max"])
+    for launch in (None, fx.Launch(mode=2)):
+        slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch)
+        assert rel_l2(slabs[-1], P) < TOL_SLICE
+        assert rel_l2(image, img) < TOL_IMAGE
+
+
+def test_diffractor_end_to_end(fx):
+    # Every GPU step from the raw section (design, t -> f, depth loop, imaging)
+    # against every oracle step.
+    w = W.DIFFRACTOR_128
+    sec = W.diffractor_section(w)
+    vm = np.full((w.nz, w.nx), 1000.0, np.float32)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    k_max = float(om[-1] / 1000.0)
+    table = O.design_operators(w.nk, k_max, w.dx, w.dz, w.L, w.theta_deg)
+    _, dk = O.k_grid(w.nk, k_max)
+    _, ref_img = O.migrate(O.band_dft(sec, w.i0, w.nw), vm, table, O.q_values(om, dk))
+    d = desc_of(fx, w, k_max)
+    img = fx.migrate_section(d, torch.from_numpy(sec.astype(np.float32)), torch.from_numpy(vm))
+    torch.cuda.synchronize()
+    img = img.numpy()
+    assert rel_l2(img, ref_img) < TOL_IMAGE
+    iz, ix = np.unravel_index(np.argmax(np.abs(img)), img.shape)
+    assert abs(ix - 64) <= 1 and abs(iz - 60) <= 1
