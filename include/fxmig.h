@@ -20,7 +20,8 @@
  *     library never allocates, frees or synchronises inside these calls (except
  *     fxmig_check, which synchronises by design); all work is enqueued
  *     asynchronously on `stream` (a cudaStream_t passed as void*, NULL = the
- *     legacy default stream).  Every call can be captured into a CUDA graph.
+ *     legacy default stream).  fxmig_design_operators, fxmig_t2f,
+ *     fxmig_migrate(_ex) and fxmig_image can be captured into a CUDA graph.
  *   - Complex numbers are interleaved (re, im) pairs of float (8 bytes,
  *     "complex64") or double (16 bytes).
  *   - Return value: FXMIG_OK (0) or a negative FXMIG_E* code.  Argument errors
@@ -172,6 +173,33 @@ int fxmig_migrate_ex(const fxmig_desc *d, const fxmig_launch *launch, void *slab
  *   image     device, out: [nz][nx] float
  * Errors: FXMIG_EINVAL. */
 int fxmig_image(const fxmig_desc *d, const float *partials, int nparts, float *image, void *stream);
+
+/* fxmig_migrate_noalloc -- the persistent depth loop without a caller workspace.
+ * The paper has no counterpart: this entry point exists for callers that can
+ * pass their own input and output buffers but cannot allocate device memory
+ * (a host application whose arena owns all device memory, a plug-in that is
+ * handed buffers but no allocator, a real-time path that must not call
+ * cudaMalloc because it may synchronise the device).  It computes exactly what
+ * fxmig_migrate_ex computes with mode FXMIG_MODE_PERSISTENT and automatic
+ * choices (same arguments, same partial-image layout and count), but keeps its
+ * scratch (status word and expanded operator table) in a fixed 1 MiB
+ * device array inside the library, held on every GPU that loads the library
+ * until the process exits.  It allocates and frees nothing.
+ *   Limit: nk * (LT + 1) * 16 + 256 <= 1 MiB, where LT is the compiled half
+ *   length (4, 8, 12, 16, 17 or 20) at or above L; e.g. nk = 1024 fits every
+ *   L <= 20.  Larger problems return FXMIG_ENOSPC without enqueuing anything.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   Sharing: all calls on a device share the one array and the last call's
+ *   contents stay in it; each call rewrites what it reads, but calls that can
+ *   overlap on the GPU (different streams, concurrent graphs) race with each
+ *   other and must be serialised by the caller.
+ *   Device-side conditions (bad velocity, bounded-wait timeout) are recorded
+ *   in the library's scratch and are not reported; check velocities first.
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA. */
+int fxmig_migrate_noalloc(const fxmig_desc *d, void *slab, const float *vel, const void *table,
+                          float *partials, int nparts, int z_begin, int z_end, void *stream);
 
 /* Waits for `stream`, then reads and returns the device status word in `ws`
  * (FXMIG_OK, FXMIG_EVELOCITY or FXMIG_ETIMEOUT); FXMIG_ECUDA if the stream

@@ -25,7 +25,7 @@ __all__ = [
     "FxmigError", "Desc", "Launch", "lib", "library_path",
     "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
     "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
-    "fxmig_check", "desc_for", "migrate_section",
+    "fxmig_check", "fxmig_migrate_noalloc", "desc_for", "migrate_section",
 ]
 
 FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
@@ -206,6 +206,23 @@ def fxmig_image(d: Desc, partials, image, stream=None) -> None:
 def fxmig_check(ws, stream=None) -> int:
     """Synchronise the stream and return the device status code (0 = ok)."""
     return int(lib().fxmig_check(_dev_ptr(ws, "ws"), _stream(stream)))
+
+
+def fxmig_migrate_noalloc(d: Desc, slab, vel, table, partials, z_begin, z_end, stream=None) -> None:
+    """fxmig_migrate without a workspace argument: the library keeps its scratch
+    in a fixed device array (for callers that cannot allocate; see fxmig.h)."""
+    torch = _torch()
+    L = lib()
+    f = L.fxmig_migrate_noalloc
+    f.argtypes = [ctypes.POINTER(Desc)] + [ctypes.c_void_p] * 4 + [ctypes.c_int] * 3 + [ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    bp = _dev_ptr(slab, "slab", torch.float32, 2 * d.nw * d.nx, complex_ok=True)
+    vp = _dev_ptr(vel, "vel", torch.float32, d.nz * d.nx)
+    tp = _dev_ptr(table, "table", torch.float32, 2 * d.nk * (d.L + 1), complex_ok=True)
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * d.nx)
+    _check(f(ctypes.byref(d), bp, vp, tp, pp, int(nparts), int(z_begin), int(z_end), _stream(stream)),
+           "fxmig_migrate_noalloc")
 
 
 # ------------------------------------------------------------------ conveniences
