@@ -100,7 +100,7 @@ int fxmig_migrate_ex(const fxmig_desc* d, const fxmig_launch* launch, void* slab
         const cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), s);
         return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate");
     }
-    const cudaError_t e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s);
+    const cudaError_t e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s, true);
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate");
 }
 

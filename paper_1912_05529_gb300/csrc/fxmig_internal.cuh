@@ -102,6 +102,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 constexpr uint32_t kWaitPolls = 1u << 22;  // try_wait suspends between polls: seconds in total
+// Halo waits: a neighbour is never more than one depth step behind, so a
+// much smaller bound still leaves orders of magnitude of slack.
+constexpr uint32_t kHaloPolls = 1u << 18;
 
 // ------------------------------------------------------------------- clusters
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -113,12 +116,46 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// Split cluster barrier: arrive (release) early, wait (acquire) later; the
+// work between the two overlaps the barrier latency.
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+// Arrive without ordering this thread's earlier memory operations (for threads
+// that wrote nothing the rest of the cluster reads after the barrier).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // Address of the same shared-memory variable in CTA `rank` of this cluster,
 // as a shared::cluster address usable with st.shared::cluster.
 __device__ __forceinline__ uint32_t map_cluster_rank(const void* p, uint32_t rank) {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
     return r;
+}
+// Remote store of 8 bytes into another CTA's shared memory that counts its
+// bytes on that CTA's mbarrier (complete_tx), so the receiver learns of the
+// data from its own barrier without any cluster-wide synchronisation.
+__device__ __forceinline__ void st_async_v2(uint32_t addr, float2 v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+                 :: "r"(addr), "f"(v.x), "f"(v.y), "r"(remote_bar) : "memory");
+}
+// Bounded wait with cluster-scope acquire (data written by other CTAs).
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 __device__ __forceinline__ void st_cluster_v2(uint32_t addr, float2 v) {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
@@ -131,6 +168,8 @@ struct MigratePlan {
     int cluster;   // persistent: CTAs per frequency group along x
     int groups;    // persistent: frequency groups; per-depth: frequency tiles
     int warps;     // warps per CTA
+    int cwarps;    // persistent: interior compute warps
+    int ewarps;    // persistent: edge warps (clusters only)
     int W;         // persistent: x segment per CTA (multiple of 8)
     int lines;     // persistent: max lines per group
     size_t smem;   // dynamic shared memory bytes per CTA
@@ -145,9 +184,12 @@ bool t2f_supported(int nt);
 
 cudaError_t launch_design(const fxmig_desc* d, void* table, void* table64, cudaStream_t s);
 cudaError_t launch_t2f(const fxmig_desc* d, const float* section, void* slab, void* ws, cudaStream_t s);
+// precompute_slowness: write fl32(1/vel) into the workspace first and stage
+// slowness rows (needs the full FXMIG_WS_MIGRATE workspace); false: convert
+// velocity rows inside the depth loop (only status + table in the workspace).
 cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* vel,
                            const void* table, float* partials, int z_begin, int z_end, void* ws,
-                           cudaStream_t s);
+                           cudaStream_t s, bool precompute_slowness);
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
                          cudaStream_t s);
 

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 
+#include "fir.cuh"
 #include "fxmig_internal.cuh"
 
 namespace fxmig_impl {
@@ -43,133 +44,157 @@ struct MigrateArgs {
     double dt, dk;
     float2* slab;           // [nw][nx]
     const float* vel;       // [nz][nx]
+    const float* slow;      // [nz][nx] fl32(1/vel) precomputed, or nullptr (converted in the kernel)
     const float4* taps;     // [nk][LT+1] as (hr, hr, hi, hi)
     float* partials;        // [G][nz][nx]
     int* status;
     int W, C, G, lines, tma_ok;
+    int cwarps, ewarps;     // persistent: interior compute warps, edge warps
     // per-depth form
     const float2* in;
     float2* out;
     int z;
 };
 
-__host__ __device__ inline int seg_phys_len(int W, int LT) { return ((W + 2 * LT + 7) >> 3) * 10; }
-__host__ __device__ inline int phys(int p) { return p + 2 * (p >> 3); }
-__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
-
-// q_w = fl32(w / dk), w = 2 pi (i0 + j) / (nt dt), evaluated in FP64 and rounded once.
-__device__ __forceinline__ float q_of_line(int i0, int j, int nt, double dt, double dk) {
-    const double w = 2.0 * 3.14159265358979323846 * (double)(i0 + j) / ((double)nt * dt);
-    return __double2float_rn(w / dk);
-}
-
-// Table index of Sec. III: nearest entry, rint_half_even(fl32(q s)), clamped.
-__device__ __forceinline__ int table_index(float q, float s, int nk) {
-    const int idx = __float2int_rn(__fmul_rn(q, s));
-    return min(max(idx, 0), nk - 1);
-}
-
-// Eq. 1 for 8 consecutive outputs.  wbase points at the padded position of
-// the first window value (x of the first output minus L).  Outputs are
-//   out_r = h0 P_r + sum_{n=1}^{L} h_n (P_{r-n} + P_{r+n}),
-// accumulated as A = sum hr * (pair) and B = sum hi * (pair) with packed
-// (re, im) f32x2 operations, then out = (A.re - B.im, A.im + B.re).
-template <int LT>
-__device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const float (&s8)[8], float q, int nk,
-                                     const float4* __restrict__ taps, u64 (&res)[8], float (&re)[8]) {
-    constexpr int NWIN = 8 + 2 * LT;
-    u64 w[NWIN];
-#pragma unroll
-    for (int t = 0; t < NWIN; t += 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(wbase + t + 2 * (t >> 3));
-        w[t] = v.x;
-        w[t + 1] = v.y;
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) re[r] = f2_unpack(w[LT + r]).x;
-    const float4* tp[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) tp[r] = taps + (size_t)table_index(q, s8[r], nk) * (LT + 1);
-    u64 A[8], B[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        u64 hr, hi;
-        ldg_nc_v2(tp[r], hr, hi);
-        A[r] = f2_mul(hr, w[LT + r]);
-        B[r] = f2_mul(hi, w[LT + r]);
-    }
-#pragma unroll
-    for (int n = 1; n <= LT; ++n) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            u64 hr, hi;
-            ldg_nc_v2(tp[r] + n, hr, hi);
-            const u64 t = f2_add(w[LT + r - n], w[LT + r + n]);
-            A[r] = f2_fma(hr, t, A[r]);
-            B[r] = f2_fma(hi, t, B[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const float2 a = f2_unpack(A[r]), b = f2_unpack(B[r]);
-        res[r] = f2_pack(a.x - b.y, a.y + b.x);
-    }
-}
-
-// Store 8 outputs at padded positions LT + r relative to the 8-aligned base.
-template <int LT>
-__device__ __forceinline__ void store8(float2* base, const u64 (&res)[8]) {
-    if constexpr ((LT & 1) == 0) {
-#pragma unroll
-        for (int r = 0; r < 8; r += 2) {
-            const int t = LT + r;
-            *reinterpret_cast<ulonglong2*>(base + t + 2 * (t >> 3)) = make_ulonglong2(res[r], res[r + 1]);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int t = LT + r;
-            *reinterpret_cast<u64*>(base + t + 2 * (t >> 3)) = res[r];
-        }
-    }
-}
-
-__device__ __forceinline__ void load_s8(const float* p, float (&s8)[8]) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    const float4 b = *reinterpret_cast<const float4*>(p + 4);
-    s8[0] = a.x; s8[1] = a.y; s8[2] = a.z; s8[3] = a.w;
-    s8[4] = b.x; s8[5] = b.y; s8[6] = b.z; s8[7] = b.w;
-}
-
 struct PersistentSmem {
-    size_t mbar, qs, vbuf, sbuf, img, wave, total;
+    size_t mbar, qs, fixc, vbuf, sbuf, img, fixl, mm, wave, total;
 };
+constexpr int kRowSlots = 3;  // ring of staged velocity/slowness rows
+constexpr int kFixCap = 96;   // operator changes per step the fixup warp takes alone
 __host__ __device__ inline PersistentSmem persistent_layout(int W, int lines, int LT) {
     PersistentSmem s;
     s.mbar = 0;
-    s.qs = 16;
-    s.vbuf = align16(s.qs + 4 * (size_t)lines);
-    s.sbuf = s.vbuf + 2 * (size_t)W * 4;
+    s.qs = 8 * (kRowSlots + 4);  // row-staging barriers, then halo barriers [side][parity]
+    s.fixc = align16(s.qs + 4 * (size_t)lines);
+    s.vbuf = s.fixc + 16;  // fix counts [2] and edge flags [2]
+    s.sbuf = s.vbuf + kRowSlots * (size_t)W * 4;
     s.img = s.sbuf + 2 * (size_t)W * 4;
-    s.wave = align16(s.img + 2 * (size_t)lines * W * 4);
+    s.fixl = s.img + 2 * (size_t)lines * W * 4;
+    s.mm = s.fixl + 2 * (size_t)kFixCap * 4;
+    s.wave = align16(s.mm + 2 * (size_t)lines * (W / 8));
     s.total = s.wave + 2 * (size_t)lines * seg_phys_len(W, LT) * 8;
     return s;
 }
 
 // ------------------------------------------------------------ persistent form
-constexpr int kPersistentMaxThreads = 384;  // 12 warps, up to 168 registers per thread
+constexpr int kPersistentMaxThreads = 512;  // up to 15 compute warps + 1 housekeeping warp (128 registers)
+
+// Per-CTA constants of the persistent kernel.
+struct SegCtx {
+    int W, SP, wv, rank, C, nk;
+    bool has_left, has_right;    // cluster neighbours exist on that side
+    uint32_t nb_left, nb_right;  // neighbours' wave base (shared::cluster address)
+    // halo barriers of the neighbours that receive this CTA's edge outputs:
+    // the left neighbour's right-halo barrier and the right neighbour's
+    // left-halo barrier, for the parity of the receiving depth step
+    uint32_t bar_left[2], bar_right[2];
+};
+
+// Send output x of line s (value v) to the neighbours whose halo holds it.
+template <int LT>
+__device__ __forceinline__ void push_halo(const SegCtx& g, size_t nxt_off, int s, int x, u64 v, int pb) {
+    if (g.has_left && x < LT)
+        st_async_v2(g.nb_left + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(g.W + LT + x)) * 8), f2_unpack(v),
+                    g.bar_left[pb]);
+    if (g.has_right && x >= g.W - LT)
+        st_async_v2(g.nb_right + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(x - g.W + LT)) * 8), f2_unpack(v),
+                    g.bar_right[pb]);
+}
+
+// Write one output (local position x of line s) to the next buffer and, when
+// `push` is set and it lies within LT of a segment edge, into the halo of the
+// neighbour on that side (st.async, counted on the neighbour's halo barrier
+// of parity pb).
+template <int LT>
+__device__ __forceinline__ void put_output(const SegCtx& g, float2* nxt, size_t nxt_off, int s, int x, u64 v,
+                                           bool push, int pb) {
+    *reinterpret_cast<u64*>(nxt + (size_t)s * g.SP + phys(x + LT)) = v;
+    if (push) push_halo<LT>(g, nxt_off, s, x, v, pb);
+}
+
+// One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
+// extrapolated with the operator of the first output.  Outputs whose own
+// operator differs (bits of `skip`) are left unwritten for fir1.  The real
+// parts of the current wavefield go to the imaging buffer.
+template <int LT>
+__device__ __forceinline__ void main_item(const SegCtx& g, int s, int xl0, uint32_t skip, bool edge, bool push,
+                                          int pb, const float2* cur, float2* nxt, size_t nxt_off,
+                                          const float* srow, const float* qs, float* imgz,
+                                          const float4* __restrict__ taps) {
+    const int idx0 = table_index(qs[s], srow[xl0], g.nk);
+    u64 res[8];
+    float re[8];
+    fir8_shared_taps<LT>(cur + (size_t)s * g.SP + (xl0 >> 3) * 10, idx0, taps, res, re);
+    *reinterpret_cast<float4*>(imgz + (size_t)s * g.W + xl0) = make_float4(re[0], re[1], re[2], re[3]);
+    *reinterpret_cast<float4*>(imgz + (size_t)s * g.W + xl0 + 4) = make_float4(re[4], re[5], re[6], re[7]);
+    if (xl0 + 8 > g.wv) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (xl0 + r >= g.wv) res[r] = 0ull;
+    }
+    if (skip == 0 && !edge) {
+        store8<LT>(nxt + (size_t)s * g.SP + (xl0 >> 3) * 10, res);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (!((skip >> r) & 1u)) put_output<LT>(g, nxt, nxt_off, s, xl0 + r, res[r], push, pb);
+    }
+}
+
+// Warp-cooperative recomputation of the outputs flagged in each lane's
+// `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
+// numbered and taken one per lane.  All 32 lanes must call.
+template <int LT>
+__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0, const float2* cur,
+                                            float2* nxt, size_t nxt_off, const float* srow, const float* qs,
+                                            const float4* __restrict__ taps, int lane, bool push, int pb) {
+    const uint32_t cnt = __popc(mask);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    const uint32_t excl = incl - cnt;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t it = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            const uint32_t ex = __shfl_sync(0xffffffffu, excl, cand);
+            if (ex <= it) owner = cand;
+        }
+        const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
+        const int s_o = __shfl_sync(0xffffffffu, s, owner);
+        const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
+        if (it < total) {
+            const int r = (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
+            const int x = x0_o + r;
+            const int idx = table_index(qs[s_o], srow[x], g.nk);
+            put_output<LT>(g, nxt, nxt_off, s_o, x, fir1<LT>(cur + (size_t)s_o * g.SP, x, idx, taps), push, pb);
+        }
+    }
+}
 
 template <int LT>
 __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = a.W, m = a.lines, C = a.C;
     const int SP = seg_phys_len(W, LT);
+    const int NC = W >> 3;
     const PersistentSmem L = persistent_layout(W, m, LT);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
     float* qs = reinterpret_cast<float*>(smem + L.qs);
+    int* fix_count = reinterpret_cast<int*>(smem + L.fixc);
     float* vbuf = reinterpret_cast<float*>(smem + L.vbuf);
     float* sbuf = reinterpret_cast<float*>(smem + L.sbuf);
     float* img = reinterpret_cast<float*>(smem + L.img);
+    uint32_t* fix_list = reinterpret_cast<uint32_t*>(smem + L.fixl);
+    unsigned char* mm = smem + L.mm;
     float2* wave = reinterpret_cast<float2*>(smem + L.wave);
 
     const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
@@ -178,15 +203,19 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     const int mg = (int)(((long long)(g + 1) * a.nw) / a.G) - l_begin;
     const int x0 = rank * W;
     const int wv = max(0, min(W, a.nx - x0));
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-    const int nchunks = (W + 255) >> 8;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    // Warp roles during a depth step: [0, cw) compute, then one fixup warp.
+    // Between steps the whole CTA reduces the image row and prepares the next.
+    const int cw = a.cwarps;
+    const bool is_comp = warp < cw;
+    const bool is_fix = warp == cw;
 
     // ---- prologue: zero both wavefield buffers (halos outside [0, nx) stay 0)
     for (int i = tid; i < 2 * m * SP; i += nthr) wave[i] = make_float2(0.f, 0.f);
     for (int s = tid; s < m; s += nthr) qs[s] = (s < mg) ? q_of_line(a.i0, l_begin + s, a.nt, a.dt, a.dk) : 0.f;
+    uint64_t* hbar = mbar + kRowSlots;  // [side 0 left, 1 right][parity]
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int b = 0; b < kRowSlots + 4; ++b) mbar_init(&mbar[b], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -200,25 +229,35 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
         }
     }
 
-    uint32_t phase = 0;  // bit b: parity of the next wait on mbar[b]
-    auto issue_row = [&](int z) {  // thread 0 only
+    // Row staging.  Row z of the slowness field (precomputed, a.slow) or of
+    // the velocity (converted here) goes through slot z % kRowSlots of vbuf by
+    // a 1-D bulk copy, issued two depth steps ahead.  The k-th use of a slot
+    // completes mbarrier phase k, so row z waits on parity ((z-z_begin)/3)&1;
+    // any thread may wait.  With precomputed slowness the depth step reads the
+    // slot directly; otherwise the CTA converts it into sbuf[z & 1].
+    const float* rows = a.slow ? a.slow : a.vel;
+    auto issue_row = [&](int z) {  // one thread
         if (!a.tma_ok) return;
-        const int b = z & 1;
+        const int b = z % kRowSlots;
         const uint32_t bytes = (uint32_t)wv * 4u;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&mbar[b], bytes);
-        if (bytes) bulk_g2s(vbuf + b * W, a.vel + (size_t)z * a.nx + x0, bytes, &mbar[b]);
+        if (bytes) bulk_g2s(vbuf + b * W, rows + (size_t)z * a.nx + x0, bytes, &mbar[b]);
     };
     auto wait_row = [&](int z) {
         if (!a.tma_ok) return;
-        const int b = z & 1;
-        if (!mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, kWaitPolls)) {
-            if (tid == 0) atomicOr(a.status, kStatusTimeout);
-        }
-        phase ^= (1u << b);
+        const int b = z % kRowSlots;
+        if (!mbar_wait_bounded(&mbar[b], (uint32_t)(((z - a.z_begin) / kRowSlots) & 1), kWaitPolls))
+            atomicOr(a.status, kStatusTimeout);
     };
-    auto convert_row = [&](int z) {  // s = fl32(1/v) for the CTA's x segment
-        const float* src = a.tma_ok ? (vbuf + (z & 1) * W) : (a.vel + (size_t)z * a.nx + x0);
+    auto srow_of = [&](int z) -> const float* {
+        if (a.slow) return a.tma_ok ? (vbuf + (z % kRowSlots) * W) : (a.slow + (size_t)z * a.nx + x0);
+        return sbuf + (z & 1) * W;
+    };
+    // s = fl32(1/v) for the CTA's x segment (only without precomputed slowness)
+    auto convert_row = [&](int z) {
+        if (a.slow) return;
+        const float* src = a.tma_ok ? (vbuf + (z % kRowSlots) * W) : (a.vel + (size_t)z * a.nx + x0);
         float* dst = sbuf + (z & 1) * W;
         bool bad = false;
         for (int x = tid; x < W; x += nthr) {
@@ -232,7 +271,8 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
         }
         if (bad) atomicOr(a.status, kStatusVelocity);
     };
-    auto reduce_image_row = [&](int zr) {  // partial[g][zr][x0 + x] = sum over lines, ascending
+    // partial[g][zr][x0 + x] = sum over the group's lines, ascending
+    auto reduce_image_row = [&](int zr) {
         const float* src = img + (size_t)(zr & 1) * m * W;
         float* dst = a.partials + ((size_t)g * a.nz + zr) * a.nx + x0;
         for (int x = tid * 4; x < wv; x += nthr * 4) {
@@ -249,75 +289,189 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
             }
         }
     };
+    // Operator-change masks of depth row zn: for every (line, chunk) pair the
+    // outputs whose table index differs from the chunk's first output, one
+    // pair per thread.  The changed outputs are also listed (line << 16 | x)
+    // for the fixup warp, with one atomic per warp; fix_count[zn & 1] (zero on
+    // entry) counts them and fix_count[2 + (zn & 1)] flags edge outputs.
+    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
+    auto build_masks = [&](int zn) {
+        const float* sr = srow_of(zn);
+        unsigned char* mmz = mm + (size_t)(zn & 1) * m * NC;
+        uint32_t* lst = fix_list + (zn & 1) * kFixCap;
+        for (int base = warp * 32; base < m * NC; base += nthr) {
+            const int p = base + lane;
+            uint32_t mask = 0;
+            int s = 0, c = 0;
+            if (p < m * NC) {
+                s = p / NC;
+                c = p - s * NC;
+                const int xl0 = c << 3;
+                if (s < mg && xl0 < wv) {
+                    float s8[8];
+                    load_s8(sr + xl0, s8);
+                    bool same = true;
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
+                    if (!same) {
+                        const int nvalid = min(8, wv - xl0);
+                        const float q = qs[s];
+                        const int i0 = table_index(q, s8[0], a.nk);
+#pragma unroll
+                        for (int r = 1; r < 8; ++r)
+                            if (r < nvalid && table_index(q, s8[r], a.nk) != i0) mask |= 1u << r;
+                    }
+                }
+                mmz[p] = (unsigned char)mask;
+            }
+            const uint32_t cnt = __popc(mask);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            int wbase = 0;
+            if (lane == 31) wbase = atomicAdd(&fix_count[zn & 1], (int)total);
+            wbase = __shfl_sync(0xffffffffu, wbase, 31);
+            const bool edge_chunk = (C > 1) && (c < E || c >= NC - E);
+            if (mask && edge_chunk) fix_count[2 + (zn & 1)] = 1;
+            uint32_t pos = (uint32_t)wbase + incl - cnt, bits = mask;
+            while (bits) {
+                const int r = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (pos < (uint32_t)kFixCap) lst[pos] = ((uint32_t)s << 16) | (uint32_t)((c << 3) + r);
+                ++pos;
+            }
+        }
+    };
 
     if (tid == 0) {
+        for (int i = 0; i < 4; ++i) fix_count[i] = 0;
         issue_row(a.z_begin);
         if (a.z_begin + 1 < a.z_end) issue_row(a.z_begin + 1);
     }
     wait_row(a.z_begin);
     convert_row(a.z_begin);
+    __syncthreads();
+    build_masks(a.z_begin);
     // every CTA of the cluster has zeroed its buffers before any halo push
     if (C > 1) cluster_sync_all(); else __syncthreads();
 
-    uint32_t nb_left = 0, nb_right = 0;  // wave base in the neighbours' shared memory
-    if (C > 1) {
-        if (rank > 0) nb_left = map_cluster_rank(wave, rank - 1);
-        if (rank < C - 1) nb_right = map_cluster_rank(wave, rank + 1);
+    SegCtx sc;
+    sc.W = W; sc.SP = SP; sc.wv = wv; sc.rank = rank; sc.C = C; sc.nk = a.nk;
+    sc.has_left = C > 1 && rank > 0;
+    sc.has_right = C > 1 && rank < C - 1;
+    sc.nb_left = sc.has_left ? map_cluster_rank(wave, rank - 1) : 0u;
+    sc.nb_right = sc.has_right ? map_cluster_rank(wave, rank + 1) : 0u;
+    for (int b = 0; b < 2; ++b) {
+        sc.bar_left[b] = sc.has_left ? map_cluster_rank(&hbar[2 + b], rank - 1) : 0u;   // its right halo
+        sc.bar_right[b] = sc.has_right ? map_cluster_rank(&hbar[b], rank + 1) : 0u;     // its left halo
     }
+    // bytes each halo barrier phase receives: LT outputs of every line
+    const uint32_t halo_bytes = (uint32_t)mg * LT * 8u;
+
+    // Work items: (line, 8-output chunk), one per compute lane and round.
+    // With a cluster, the chunks within LT of a segment edge ("edge" chunks)
+    // read the halo, send their outputs to the neighbours' halos and fix
+    // their own operator changes; the fixup warp takes the interior ones.
+    // Halo exchange is point to point: outputs go out with st.async, and a
+    // CTA waits on its own halo barrier of the step's parity before it reads
+    // its halo; the neighbours can never be more than one step apart, so two
+    // parities suffice and no cluster-wide barrier is needed.
+    const int n_items = mg * NC;
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
         const float2* cur = wave + (size_t)zb * m * SP;
         float2* nxt = wave + (size_t)(zb ^ 1) * m * SP;
         const size_t nxt_off = (size_t)(zb ^ 1) * m * SP;
-        if (z > a.z_begin) reduce_image_row(z - 1);
-
-        const float* srow = sbuf + (z & 1) * W;
+        const float* srow = srow_of(z);
         float* imgz = img + (size_t)(z & 1) * m * W;
-        for (int task = warp; task < mg * nchunks; task += nwarps) {
-            const int s = task / nchunks;
-            const int xl0 = (task - s * nchunks) * 256 + lane * 8;
-            if (xl0 >= W) continue;
-            float s8[8], re[8];
-            u64 res[8];
-            load_s8(srow + xl0, s8);
-            fir8<LT>(cur + (size_t)s * SP + (xl0 >> 3) * 10, s8, qs[s], a.nk, a.taps, res, re);
-            *reinterpret_cast<float4*>(imgz + (size_t)s * W + xl0) = make_float4(re[0], re[1], re[2], re[3]);
-            *reinterpret_cast<float4*>(imgz + (size_t)s * W + xl0 + 4) = make_float4(re[4], re[5], re[6], re[7]);
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-                if (xl0 + r >= wv) res[r] = 0ull;
-            store8<LT>(nxt + (size_t)s * SP + (xl0 >> 3) * 10, res);
-            if (C > 1) {
-                if (rank > 0 && xl0 < LT) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const int x = xl0 + r;
-                        if (x < LT)
-                            st_cluster_v2(nb_left + (uint32_t)((nxt_off + (size_t)s * SP + phys(W + LT + x)) * 8),
-                                          f2_unpack(res[r]));
-                    }
-                }
-                if (rank < C - 1 && xl0 + 8 > W - LT) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const int x = xl0 + r;
-                        if (x >= W - LT)
-                            st_cluster_v2(nb_right + (uint32_t)((nxt_off + (size_t)s * SP + phys(x - W + LT)) * 8),
-                                          f2_unpack(res[r]));
-                    }
-                }
+        const unsigned char* mmz = mm + (size_t)(z & 1) * m * NC;
+        const int nfix = fix_count[z & 1];
+        const bool push = (C > 1) && (z + 1 < a.z_end);  // outputs feed a further step
+        const int pb = (z + 1) & 1;                         // receivers' barrier parity
+        const bool halo_wait = (C > 1) && (z > a.z_begin);
+        const uint32_t hpar = (uint32_t)(((z - a.z_begin - 1) >> 1) & 1);
+        if (tid == 0) {
+            fix_count[(z + 1) & 1] = 0;  // read last at step z-1
+            fix_count[2 + ((z + 1) & 1)] = 0;
+            if (halo_wait) {
+                if (sc.has_left) mbar_arrive_expect_tx(&hbar[z & 1], halo_bytes);
+                if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes);
             }
         }
+
+        const bool inline_fix = nfix > kFixCap;  // too many for the fixup warp alone
+        if (is_comp) {
+            for (int base = warp * 32; base < n_items; base += cw * 32) {
+                const int item = base + lane;
+                int s = 0, xl0 = 0;
+                uint32_t mask = 0;
+                bool work = false, edge = false;
+                if (item < n_items) {
+                    s = item / NC;
+                    const int c = item - s * NC;
+                    xl0 = c << 3;
+                    work = xl0 < wv;
+                    edge = (C > 1) && (c < E || c >= NC - E);
+                    if (work) mask = mmz[(size_t)s * NC + c];
+                }
+                if (halo_wait && __any_sync(0xffffffffu, edge)) {
+                    // the neighbours' outputs of step z-1 have landed in cur's halo
+                    bool ok = true;
+                    if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                    if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                    if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+                }
+                if (work) {
+                    main_item<LT>(sc, s, xl0, mask, edge, push, pb, cur, nxt, nxt_off, srow, qs, imgz, a.taps);
+                } else if (edge && push && item < n_items) {
+                    // beyond the line end: the neighbours still expect zeros
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) push_halo<LT>(sc, nxt_off, s, xl0 + r, 0ull, pb);
+                }
+                if (inline_fix && __any_sync(0xffffffffu, mask != 0u))
+                    coop_fixups<LT>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, a.taps, lane, push, pb);
+            }
+        } else if (is_fix && !inline_fix && nfix > 0) {
+            // the listed operator changes of the step, one output per lane
+            if (halo_wait && fix_count[2 + (z & 1)]) {
+                bool ok = true;
+                if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+            }
+            const uint32_t* lst = fix_list + (z & 1) * kFixCap;
+            for (int i = lane; i < nfix; i += 32) {
+                const uint32_t e = lst[i];
+                const int s = (int)(e >> 16), x = (int)(e & 0xffffu);
+                const int idx = table_index(qs[s], srow[x], a.nk);
+                put_output<LT>(sc, nxt, nxt_off, s, x, fir1<LT>(cur + (size_t)s * SP, x, idx, a.taps), push, pb);
+            }
+        }
+        __syncthreads();
+        // between steps, the whole CTA: image row z, next row's masks, and
+        // the copy of row z+2 (its slot held row z-1, read by nobody now)
+        if (tid == 0 && z + 2 < a.z_end) issue_row(z + 2);
+        reduce_image_row(z);
         if (z + 1 < a.z_end) {
             wait_row(z + 1);
-            convert_row(z + 1);
+            if (!a.slow) {
+                convert_row(z + 1);
+                __syncthreads();
+            }
+            build_masks(z + 1);
         }
-        if (tid == 0 && z + 2 < a.z_end) issue_row(z + 2);
-        if (C > 1) cluster_sync_all(); else __syncthreads();
+        __syncthreads();
     }
+    // nothing is pushed at the last step and every earlier push has been
+    // waited for; the final cluster barrier only keeps the CTAs' exits ordered
+    if (C > 1) cluster_sync_all();
 
-    reduce_image_row(a.z_end - 1);
     const float2* fin = wave + (size_t)((a.z_end - a.z_begin) & 1) * m * SP;
     for (int s = 0; s < mg; ++s) {
         float2* dst = a.slab + (size_t)(l_begin + s) * a.nx + x0;
@@ -389,6 +543,18 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_migrate_step(const MigrateA
     }
 }
 
+// Slowness field s = fl32(1/v) of every velocity sample (one pass per call,
+// so the depth loop never divides); flags samples that are not finite and > 0.
+__global__ void k_slowness(const float* __restrict__ vel, size_t n, float* __restrict__ slow, int* status) {
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = vel[i];
+        bad |= !(v > 0.f && v <= FLT_MAX);
+        slow[i] = __frcp_rn(v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusVelocity);
+}
+
 // Expand the public [nk][L+1] complex64 table into the kernel layout
 // [nk][LT+1] of (hr, hr, hi, hi), zero taps beyond L.
 __global__ void k_expand_taps(const float2* __restrict__ table, int nk, int L, int LT, float4* __restrict__ taps) {
@@ -408,8 +574,9 @@ size_t migrate_ws_bytes(const fxmig_desc* d) {
     const int LT = compiled_half_length(d->L);
     if (LT < 0) return 0;
     const size_t taps = align16((size_t)d->nk * (LT + 1) * 16);
+    const size_t slow = (size_t)d->nz * d->nx * 4;
     const size_t slab2 = (size_t)d->nw * d->nx * 8;
-    return kStatusBytes + ((taps + 255) & ~size_t(255)) + slab2;
+    return kStatusBytes + ((taps + 255) & ~size_t(255)) + ((slow + 255) & ~size_t(255)) + slab2;
 }
 
 static int device_sms() {
@@ -449,6 +616,8 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
     const int smax = device_smem_optin();
     const int req_c = (launch && launch->cluster > 0) ? launch->cluster : 0;
     if (req_c && req_c != 1 && req_c != 2 && req_c != 4 && req_c != 8) return FXMIG_EINVAL;
+    const int max_warps = kPersistentMaxThreads / 32;
+    if (launch && launch->warps > 0 && (launch->warps > max_warps || launch->warps < 2)) return FXMIG_EINVAL;
     double best = 1e300;
     bool found = false;
     for (int C : {1, 2, 4, 8}) {
@@ -463,9 +632,26 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
         const size_t smem = persistent_layout(W, lines, LT).total;
         if (smem > (size_t)smax) continue;
         const int waves = (G * C + sms - 1) / sms;
-        // time model: per-step work of the busiest CTA plus the barrier cost
-        // (a cluster barrier costs about as much as ~900 points of work)
-        const double t = (double)waves * ((double)lines * W + (C > 1 ? 900.0 : 80.0));
+        // lane items: 8 outputs of one line; compute warps with the fewest
+        // idle lanes (ties: more warps), plus one fixup warp
+        const long items = (long)lines * (W / 8);
+        int cw = 0;
+        double eff_best = -1.0;
+        for (int c = max_warps - 1; c >= 1; --c) {
+            if (launch && launch->warps > 0 && c + 1 != launch->warps) continue;
+            const long rounds = std::max(1L, (items + 32L * c - 1) / (32L * c));
+            const double eff = (double)items / (double)(rounds * 32L * c);
+            if (eff > eff_best + 1e-9) { eff_best = eff; cw = c; }
+        }
+        if (!cw) continue;
+        const long rounds = std::max(1L, (items + 32L * cw - 1) / (32L * cw));
+        // time per depth step (SM cycles): FP32-pipe work of the busiest CTA
+        // (~880 cycles per warp item on one SM sub-partition, 4 per SM),
+        // bounded below by one item latency per round, plus the between-step
+        // work and barriers
+        const double work = (double)items / 32.0 * 880.0 / 4.0;
+        const double lat = (double)rounds * 3000.0;
+        const double t = (double)waves * (std::max(work, lat) + (C > 1 ? 900.0 : 600.0));
         if (t < best) {
             best = t;
             found = true;
@@ -474,9 +660,9 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
             p->W = W;
             p->lines = lines;
             p->smem = smem;
-            const int tasks = lines * ((W + 255) >> 8);
-            int warps = (launch && launch->warps > 0) ? launch->warps : std::min(12, std::max(4, tasks));
-            p->warps = std::min(warps, kPersistentMaxThreads / 32);
+            p->warps = cw + 1;
+            p->cwarps = cw;
+            p->ewarps = 0;
             p->nparts = G;
         }
     }
@@ -527,19 +713,33 @@ static cudaError_t launch_lt(const MigratePlan& plan, MigrateArgs a, cudaStream_
 
 cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* vel,
                            const void* table, float* partials, int z_begin, int z_end, void* ws,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool precompute_slowness) {
     const int LT = plan.LT;
     unsigned char* wsb = static_cast<unsigned char*>(ws);
     int* status = reinterpret_cast<int*>(wsb);
     float4* taps = reinterpret_cast<float4*>(wsb + kStatusBytes);
     const size_t taps_bytes = (align16((size_t)d->nk * (LT + 1) * 16) + 255) & ~size_t(255);
-    float2* ws_slab = reinterpret_cast<float2*>(wsb + kStatusBytes + taps_bytes);
+    const size_t slow_bytes = ((size_t)d->nz * d->nx * 4 + 255) & ~size_t(255);
+    float* slow = reinterpret_cast<float*>(wsb + kStatusBytes + taps_bytes);
+    float2* ws_slab = reinterpret_cast<float2*>(wsb + kStatusBytes + taps_bytes + slow_bytes);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     const int n = d->nk * (LT + 1);
     k_expand_taps<<<(n + 255) / 256, 256, 0, s>>>(static_cast<const float2*>(table), d->nk, d->L, LT, taps);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const bool use_slow = precompute_slowness && plan.mode == FXMIG_MODE_PERSISTENT;
+    if (use_slow) {
+        // only the rows this call reads
+        const size_t n_rows = (size_t)(z_end - z_begin) * d->nx;
+        const int sms = device_sms();
+        size_t blocks = (n_rows + 255) / 256;
+        if (blocks > (size_t)sms * 8) blocks = (size_t)sms * 8;
+        k_slowness<<<(unsigned)blocks, 256, 0, s>>>(vel + (size_t)z_begin * d->nx, n_rows,
+                                                    slow + (size_t)z_begin * d->nx, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     MigrateArgs a = {};
     a.nx = d->nx; a.nz = d->nz; a.nw = d->nw; a.nk = d->nk;
     a.z_begin = z_begin; a.z_end = z_end; a.i0 = d->i0; a.nt = d->nt;
@@ -547,11 +747,13 @@ cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* s
     a.dk = d->nk > 1 ? d->k_max / (double)(d->nk - 1) : 0.0;
     a.slab = static_cast<float2*>(slab);
     a.vel = vel;
+    a.slow = use_slow ? slow : nullptr;
     a.taps = taps;
     a.partials = partials;
     a.status = status;
     a.W = plan.W; a.C = plan.cluster; a.G = plan.groups; a.lines = plan.lines;
-    a.tma_ok = ((d->nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(vel) & 15) == 0);
+    a.cwarps = plan.cwarps; a.ewarps = plan.ewarps;
+    a.tma_ok = ((d->nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(use_slow ? (const float*)slow : vel) & 15) == 0);
     switch (LT) {
         case 4: return launch_lt<4>(plan, a, s, ws_slab);
         case 8: return launch_lt<8>(plan, a, s, ws_slab);

@@ -71,6 +71,6 @@ extern "C" int fxmig_migrate_noalloc(const fxmig_desc* d, void* slab, const floa
     if (z_begin == z_end) return FXMIG_OK;
     // launch_migrate clears the status word and rewrites the table region on
     // every call, so stale contents from an earlier call are never read.
-    e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s);
+    e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s, false);
     return e == cudaSuccess ? FXMIG_OK : FXMIG_ECUDA;
 }
