@@ -120,6 +120,25 @@ def k_max_of(w: W.Workload, vm_min: float) -> float:
     return 2.0 * math.pi * (w.i0 + w.nw - 1) / (w.nt * w.dt) / vm_min
 
 
+def kernel_traffic(workload: str):
+    """DRAM bytes per launch of the persistent depth-loop kernel from the ncu
+    capture recorded under profiles/, or None if the kernel sources changed
+    since that capture (or none exists for this workload)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_k_migrate_persistent_{workload}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for rel in ("paper_1912_05529_gb300/csrc/migrate.cu", "paper_1912_05529_gb300/csrc/fir.cuh",
+                "paper_1912_05529_gb300/csrc/fxmig_internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return rec.get("dram_bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -292,14 +311,17 @@ def run_native(args, w):
                    "l2": "flushed between steps (256 MiB write)", "partials": nparts,
                    "parallelism": f"{world} independent lines" if world > 1 else "1 line"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops,
+                     "traffic": kernel_traffic(w.name) if args.mode != 2 else None,
                      "kernel": "k_migrate_persistent" if args.mode != 2 else "k_migrate_step",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz ({peak_src} max clock)",
                      "flops_per_point": flops_per_point(w.L), "migrate_ms": mig_avg},
         "e2e": {"value": e2e_val, "unit": "point*freq/s",
                 "h2d_bytes_per_step": int(sec.nbytes + vm.nbytes), "d2h_bytes_per_step": int(d.nz * d.nx * 4),
                 "includes": "H2D section+velocity, t->f, depth loop, imaging, D2H image (table resident)"},
-        "gpu_launches": 3 * args.steps,
+        # per timed step: table expansion, slowness, depth loop, image (persistent);
+        # table expansion, one launch per depth row, image (per-depth form)
+        "gpu_launches": (4 if args.mode != 2 else 2 + d.nz) * args.steps,
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
