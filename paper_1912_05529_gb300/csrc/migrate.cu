@@ -57,27 +57,24 @@ struct MigrateArgs {
 };
 
 struct PersistentSmem {
-    size_t mbar, qs, fixc, vbuf, sbuf, img, fixl, mm, wave, total;
+    size_t mbar, qs, vbuf, sbuf, img, wave, total;
 };
-constexpr int kRowSlots = 3;  // ring of staged velocity/slowness rows
-constexpr int kFixCap = 96;   // operator changes per step the fixup warp takes alone
+constexpr int kRowSlots = 7;  // ring of staged slowness/velocity rows
+constexpr int kRowAhead = kRowSlots - 1;  // rows are staged this many depth steps ahead
 __host__ __device__ inline PersistentSmem persistent_layout(int W, int lines, int LT) {
     PersistentSmem s;
     s.mbar = 0;
     s.qs = 8 * (kRowSlots + 4);  // row-staging barriers, then halo barriers [side][parity]
-    s.fixc = align16(s.qs + 4 * (size_t)lines);
-    s.vbuf = s.fixc + 16;  // fix counts [2] and edge flags [2]
+    s.vbuf = align16(s.qs + 4 * (size_t)lines);
     s.sbuf = s.vbuf + kRowSlots * (size_t)W * 4;
     s.img = s.sbuf + 2 * (size_t)W * 4;
-    s.fixl = s.img + 2 * (size_t)lines * W * 4;
-    s.mm = s.fixl + 2 * (size_t)kFixCap * 4;
-    s.wave = align16(s.mm + 2 * (size_t)lines * (W / 8));
+    s.wave = align16(s.img + 2 * (size_t)lines * W * 4);
     s.total = s.wave + 2 * (size_t)lines * seg_phys_len(W, LT) * 8;
     return s;
 }
 
 // ------------------------------------------------------------ persistent form
-constexpr int kPersistentMaxThreads = 512;  // up to 15 compute warps + 1 housekeeping warp (128 registers)
+constexpr int kPersistentMaxThreads = 384;  // up to 12 warps: 168 registers per thread
 
 // Per-CTA constants of the persistent kernel.
 struct SegCtx {
@@ -113,15 +110,28 @@ __device__ __forceinline__ void put_output(const SegCtx& g, float2* nxt, size_t 
 }
 
 // One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
-// extrapolated with the operator of the first output.  Outputs whose own
-// operator differs (bits of `skip`) are left unwritten for fir1.  The real
-// parts of the current wavefield go to the imaging buffer.
+// extrapolated with the operator of the first output.  Returns the mask of
+// outputs whose own operator differs (the velocity changes inside the 8):
+// those are left unwritten for fir1.  The real parts of the current wavefield
+// go to the imaging buffer.
 template <int LT>
-__device__ __forceinline__ void main_item(const SegCtx& g, int s, int xl0, uint32_t skip, bool edge, bool push,
-                                          int pb, const float2* cur, float2* nxt, size_t nxt_off,
-                                          const float* srow, const float* qs, float* imgz,
-                                          const float4* __restrict__ taps) {
-    const int idx0 = table_index(qs[s], srow[xl0], g.nk);
+__device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, bool edge, bool push, int pb,
+                                              const float2* cur, float2* nxt, size_t nxt_off, const float* srow,
+                                              const float* qs, float* imgz, const float4* __restrict__ taps) {
+    float s8[8];
+    load_s8(srow + xl0, s8);
+    const float q = qs[s];
+    const int idx0 = table_index(q, s8[0], g.nk);
+    uint32_t skip = 0;
+    bool same = true;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
+    if (!same) {
+        const int nvalid = min(8, g.wv - xl0);
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+            if (r < nvalid && table_index(q, s8[r], g.nk) != idx0) skip |= 1u << r;
+    }
     u64 res[8];
     float re[8];
     fir8_shared_taps<LT>(cur + (size_t)s * g.SP + (xl0 >> 3) * 10, idx0, taps, res, re);
@@ -132,13 +142,18 @@ __device__ __forceinline__ void main_item(const SegCtx& g, int s, int xl0, uint3
         for (int r = 0; r < 8; ++r)
             if (xl0 + r >= g.wv) res[r] = 0ull;
     }
-    if (skip == 0 && !edge) {
+    if (skip == 0) {
         store8<LT>(nxt + (size_t)s * g.SP + (xl0 >> 3) * 10, res);
+        if (edge && push) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) push_halo<LT>(g, nxt_off, s, xl0 + r, res[r], pb);
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-            if (!((skip >> r) & 1u)) put_output<LT>(g, nxt, nxt_off, s, xl0 + r, res[r], push, pb);
+            if (!((skip >> r) & 1u)) put_output<LT>(g, nxt, nxt_off, s, xl0 + r, res[r], edge && push, pb);
     }
+    return skip;
 }
 
 // Warp-cooperative recomputation of the outputs flagged in each lane's
@@ -189,12 +204,9 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     const PersistentSmem L = persistent_layout(W, m, LT);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
     float* qs = reinterpret_cast<float*>(smem + L.qs);
-    int* fix_count = reinterpret_cast<int*>(smem + L.fixc);
     float* vbuf = reinterpret_cast<float*>(smem + L.vbuf);
     float* sbuf = reinterpret_cast<float*>(smem + L.sbuf);
     float* img = reinterpret_cast<float*>(smem + L.img);
-    uint32_t* fix_list = reinterpret_cast<uint32_t*>(smem + L.fixl);
-    unsigned char* mm = smem + L.mm;
     float2* wave = reinterpret_cast<float2*>(smem + L.wave);
 
     const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
@@ -204,11 +216,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     const int x0 = rank * W;
     const int wv = max(0, min(W, a.nx - x0));
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    // Warp roles during a depth step: [0, cw) compute, then one fixup warp.
-    // Between steps the whole CTA reduces the image row and prepares the next.
-    const int cw = a.cwarps;
-    const bool is_comp = warp < cw;
-    const bool is_fix = warp == cw;
+    const int nwarps = nthr >> 5;
 
     // ---- prologue: zero both wavefield buffers (halos outside [0, nx) stay 0)
     for (int i = tid; i < 2 * m * SP; i += nthr) wave[i] = make_float2(0.f, 0.f);
@@ -231,10 +239,9 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
 
     // Row staging.  Row z of the slowness field (precomputed, a.slow) or of
     // the velocity (converted here) goes through slot z % kRowSlots of vbuf by
-    // a 1-D bulk copy, issued two depth steps ahead.  The k-th use of a slot
-    // completes mbarrier phase k, so row z waits on parity ((z-z_begin)/3)&1;
-    // any thread may wait.  With precomputed slowness the depth step reads the
-    // slot directly; otherwise the CTA converts it into sbuf[z & 1].
+    // a 1-D bulk copy, issued kRowAhead depth steps ahead.  The k-th use of a
+    // slot completes mbarrier phase k, so row z waits on parity
+    // ((z - z_begin) / kRowSlots) & 1; every thread that reads the row waits.
     const float* rows = a.slow ? a.slow : a.vel;
     auto issue_row = [&](int z) {  // one thread
         if (!a.tma_ok) return;
@@ -289,74 +296,11 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
             }
         }
     };
-    // Operator-change masks of depth row zn: for every (line, chunk) pair the
-    // outputs whose table index differs from the chunk's first output, one
-    // pair per thread.  The changed outputs are also listed (line << 16 | x)
-    // for the fixup warp, with one atomic per warp; fix_count[zn & 1] (zero on
-    // entry) counts them and fix_count[2 + (zn & 1)] flags edge outputs.
-    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
-    auto build_masks = [&](int zn) {
-        const float* sr = srow_of(zn);
-        unsigned char* mmz = mm + (size_t)(zn & 1) * m * NC;
-        uint32_t* lst = fix_list + (zn & 1) * kFixCap;
-        for (int base = warp * 32; base < m * NC; base += nthr) {
-            const int p = base + lane;
-            uint32_t mask = 0;
-            int s = 0, c = 0;
-            if (p < m * NC) {
-                s = p / NC;
-                c = p - s * NC;
-                const int xl0 = c << 3;
-                if (s < mg && xl0 < wv) {
-                    float s8[8];
-                    load_s8(sr + xl0, s8);
-                    bool same = true;
-#pragma unroll
-                    for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
-                    if (!same) {
-                        const int nvalid = min(8, wv - xl0);
-                        const float q = qs[s];
-                        const int i0 = table_index(q, s8[0], a.nk);
-#pragma unroll
-                        for (int r = 1; r < 8; ++r)
-                            if (r < nvalid && table_index(q, s8[r], a.nk) != i0) mask |= 1u << r;
-                    }
-                }
-                mmz[p] = (unsigned char)mask;
-            }
-            const uint32_t cnt = __popc(mask);
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            if (total == 0) continue;
-            int wbase = 0;
-            if (lane == 31) wbase = atomicAdd(&fix_count[zn & 1], (int)total);
-            wbase = __shfl_sync(0xffffffffu, wbase, 31);
-            const bool edge_chunk = (C > 1) && (c < E || c >= NC - E);
-            if (mask && edge_chunk) fix_count[2 + (zn & 1)] = 1;
-            uint32_t pos = (uint32_t)wbase + incl - cnt, bits = mask;
-            while (bits) {
-                const int r = __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (pos < (uint32_t)kFixCap) lst[pos] = ((uint32_t)s << 16) | (uint32_t)((c << 3) + r);
-                ++pos;
-            }
-        }
-    };
 
-    if (tid == 0) {
-        for (int i = 0; i < 4; ++i) fix_count[i] = 0;
-        issue_row(a.z_begin);
-        if (a.z_begin + 1 < a.z_end) issue_row(a.z_begin + 1);
-    }
+    if (tid == 0)
+        for (int zz = a.z_begin; zz < min(a.z_end, a.z_begin + kRowAhead); ++zz) issue_row(zz);
     wait_row(a.z_begin);
     convert_row(a.z_begin);
-    __syncthreads();
-    build_masks(a.z_begin);
     // every CTA of the cluster has zeroed its buffers before any halo push
     if (C > 1) cluster_sync_all(); else __syncthreads();
 
@@ -373,14 +317,15 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     // bytes each halo barrier phase receives: LT outputs of every line
     const uint32_t halo_bytes = (uint32_t)mg * LT * 8u;
 
-    // Work items: (line, 8-output chunk), one per compute lane and round.
-    // With a cluster, the chunks within LT of a segment edge ("edge" chunks)
-    // read the halo, send their outputs to the neighbours' halos and fix
-    // their own operator changes; the fixup warp takes the interior ones.
-    // Halo exchange is point to point: outputs go out with st.async, and a
-    // CTA waits on its own halo barrier of the step's parity before it reads
-    // its halo; the neighbours can never be more than one step apart, so two
-    // parities suffice and no cluster-wide barrier is needed.
+    // Work items: (line, 8-output chunk), one per lane and round.  Chunks
+    // within LT of a segment edge ("edge" chunks) read the halo and send their
+    // outputs to the neighbours' halos.  Halo exchange is point to point:
+    // outputs go out with st.async, and a CTA waits on its own halo barrier
+    // of the step's parity before it reads its halo; neighbours can never be
+    // more than one step apart, so two parities suffice and no cluster-wide
+    // barrier is needed.  One CTA barrier ends a depth step; the image row of
+    // the step is reduced right after it, overlapping the next step's items.
+    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
     const int n_items = mg * NC;
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
@@ -390,87 +335,60 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
         const size_t nxt_off = (size_t)(zb ^ 1) * m * SP;
         const float* srow = srow_of(z);
         float* imgz = img + (size_t)(z & 1) * m * W;
-        const unsigned char* mmz = mm + (size_t)(z & 1) * m * NC;
-        const int nfix = fix_count[z & 1];
         const bool push = (C > 1) && (z + 1 < a.z_end);  // outputs feed a further step
         const int pb = (z + 1) & 1;                         // receivers' barrier parity
         const bool halo_wait = (C > 1) && (z > a.z_begin);
         const uint32_t hpar = (uint32_t)(((z - a.z_begin - 1) >> 1) & 1);
         if (tid == 0) {
-            fix_count[(z + 1) & 1] = 0;  // read last at step z-1
-            fix_count[2 + ((z + 1) & 1)] = 0;
+            // row z+kRowAhead goes to the slot of row z-1, which nobody reads now
+            if (z + kRowAhead < a.z_end) issue_row(z + kRowAhead);
             if (halo_wait) {
                 if (sc.has_left) mbar_arrive_expect_tx(&hbar[z & 1], halo_bytes);
                 if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes);
             }
         }
+        if (a.slow && z > a.z_begin) wait_row(z);  // (converted rows were synchronised)
 
-        const bool inline_fix = nfix > kFixCap;  // too many for the fixup warp alone
-        if (is_comp) {
-            for (int base = warp * 32; base < n_items; base += cw * 32) {
-                const int item = base + lane;
-                int s = 0, xl0 = 0;
-                uint32_t mask = 0;
-                bool work = false, edge = false;
-                if (item < n_items) {
-                    s = item / NC;
-                    const int c = item - s * NC;
-                    xl0 = c << 3;
-                    work = xl0 < wv;
-                    edge = (C > 1) && (c < E || c >= NC - E);
-                    if (work) mask = mmz[(size_t)s * NC + c];
-                }
-                if (halo_wait && __any_sync(0xffffffffu, edge)) {
-                    // the neighbours' outputs of step z-1 have landed in cur's halo
-                    bool ok = true;
-                    if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
-                    if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
-                    if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
-                }
-                if (work) {
-                    main_item<LT>(sc, s, xl0, mask, edge, push, pb, cur, nxt, nxt_off, srow, qs, imgz, a.taps);
-                } else if (edge && push && item < n_items) {
-                    // beyond the line end: the neighbours still expect zeros
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) push_halo<LT>(sc, nxt_off, s, xl0 + r, 0ull, pb);
-                }
-                if (inline_fix && __any_sync(0xffffffffu, mask != 0u))
-                    coop_fixups<LT>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, a.taps, lane, push, pb);
+        for (int base = warp * 32; base < n_items; base += nwarps * 32) {
+            const int item = base + lane;
+            int s = 0, xl0 = 0;
+            bool work = false, edge = false;
+            if (item < n_items) {
+                s = item / NC;
+                const int c = item - s * NC;
+                xl0 = c << 3;
+                work = xl0 < wv;
+                edge = (C > 1) && (c < E || c >= NC - E);
             }
-        } else if (is_fix && !inline_fix && nfix > 0) {
-            // the listed operator changes of the step, one output per lane
-            if (halo_wait && fix_count[2 + (z & 1)]) {
+            if (halo_wait && __any_sync(0xffffffffu, edge)) {
+                // the neighbours' outputs of step z-1 have landed in cur's halo
                 bool ok = true;
                 if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
                 if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
-            const uint32_t* lst = fix_list + (z & 1) * kFixCap;
-            for (int i = lane; i < nfix; i += 32) {
-                const uint32_t e = lst[i];
-                const int s = (int)(e >> 16), x = (int)(e & 0xffffu);
-                const int idx = table_index(qs[s], srow[x], a.nk);
-                put_output<LT>(sc, nxt, nxt_off, s, x, fir1<LT>(cur + (size_t)s * SP, x, idx, a.taps), push, pb);
+            uint32_t mask = 0;
+            if (work) {
+                mask = main_item<LT>(sc, s, xl0, edge, push, pb, cur, nxt, nxt_off, srow, qs, imgz, a.taps);
+            } else if (edge && push && item < n_items) {
+                // beyond the line end: the neighbours still expect zeros
+#pragma unroll
+                for (int r = 0; r < 8; ++r) push_halo<LT>(sc, nxt_off, s, xl0 + r, 0ull, pb);
             }
+            if (__any_sync(0xffffffffu, mask != 0u))
+                coop_fixups<LT>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, a.taps, lane, push, pb);
         }
-        __syncthreads();
-        // between steps, the whole CTA: image row z, next row's masks, and
-        // the copy of row z+2 (its slot held row z-1, read by nobody now)
-        if (tid == 0 && z + 2 < a.z_end) issue_row(z + 2);
-        reduce_image_row(z);
-        if (z + 1 < a.z_end) {
+        if (!a.slow && z + 1 < a.z_end) {
+            // velocity rows are converted by the whole CTA before the next step
             wait_row(z + 1);
-            if (!a.slow) {
-                convert_row(z + 1);
-                __syncthreads();
-            }
-            build_masks(z + 1);
+            convert_row(z + 1);
         }
         __syncthreads();
+        reduce_image_row(z);  // img[z & 1] is next written at step z + 2
     }
     // nothing is pushed at the last step and every earlier push has been
-    // waited for; the final cluster barrier only keeps the CTAs' exits ordered
-    if (C > 1) cluster_sync_all();
+    // waited for; the final barrier keeps the CTAs' exits ordered
+    if (C > 1) cluster_sync_all(); else __syncthreads();
 
     const float2* fin = wave + (size_t)((a.z_end - a.z_begin) & 1) * m * SP;
     for (int s = 0; s < mg; ++s) {
@@ -617,7 +535,7 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
     const int req_c = (launch && launch->cluster > 0) ? launch->cluster : 0;
     if (req_c && req_c != 1 && req_c != 2 && req_c != 4 && req_c != 8) return FXMIG_EINVAL;
     const int max_warps = kPersistentMaxThreads / 32;
-    if (launch && launch->warps > 0 && (launch->warps > max_warps || launch->warps < 2)) return FXMIG_EINVAL;
+    if (launch && launch->warps > 0 && (launch->warps > max_warps || launch->warps < 1)) return FXMIG_EINVAL;
     double best = 1e300;
     bool found = false;
     for (int C : {1, 2, 4, 8}) {
@@ -632,13 +550,13 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
         const size_t smem = persistent_layout(W, lines, LT).total;
         if (smem > (size_t)smax) continue;
         const int waves = (G * C + sms - 1) / sms;
-        // lane items: 8 outputs of one line; compute warps with the fewest
-        // idle lanes (ties: more warps), plus one fixup warp
+        // lane items: 8 outputs of one line; the warp count with the fewest
+        // idle lanes (ties: more warps)
         const long items = (long)lines * (W / 8);
         int cw = 0;
         double eff_best = -1.0;
-        for (int c = max_warps - 1; c >= 1; --c) {
-            if (launch && launch->warps > 0 && c + 1 != launch->warps) continue;
+        for (int c = max_warps; c >= 1; --c) {
+            if (launch && launch->warps > 0 && c != launch->warps) continue;
             const long rounds = std::max(1L, (items + 32L * c - 1) / (32L * c));
             const double eff = (double)items / (double)(rounds * 32L * c);
             if (eff > eff_best + 1e-9) { eff_best = eff; cw = c; }
@@ -660,7 +578,7 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
             p->W = W;
             p->lines = lines;
             p->smem = smem;
-            p->warps = cw + 1;
+            p->warps = cw;
             p->cwarps = cw;
             p->ewarps = 0;
             p->nparts = G;
