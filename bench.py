@@ -39,12 +39,12 @@ NOMINAL_SMS = 152
 NOMINAL_SM_MHZ = 2070.0
 
 
-def flops_per_point(L: int) -> int:
-    """Algorithmic FP32 flops per extrapolated point x frequency (Eq. 1 with
-    symmetric taps): L complex pair additions (2L), one complex product (6),
-    L complex multiply-adds (8L), the imaging addition (1) and the table-index
-    product (1): 10L + 8."""
-    return 10 * L + 8
+def ops_per_point(L: int) -> int:
+    """Algorithmic FP32 operations per extrapolated point x frequency, each
+    occupying one FP32 lane slot (an FMA counts once): L complex pair additions
+    (2L), the L+1 complex multiply-adds of Eq. 1 with symmetric taps (4(L+1)):
+    6L + 4.  (In flops, FMA = 2: 10L + 6.)"""
+    return 6 * L + 4
 
 
 def env_rank():
@@ -297,9 +297,11 @@ def run_native(args, w):
     sm_max = float(peaks.get("sm_max_mhz", NOMINAL_SM_MHZ))
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
-    peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    # FP32 pipe: 128 lanes per SM, one operation per lane per cycle (packed
+    # f32x2 instructions take two cycles), at the maximum SM clock
+    peak_tops = sms * 128 * sm_max * 1e6 / 1e12
     mig_avg = sum(mig_ms) / len(mig_ms)
-    achieved = flops_per_point(w.L) * w.points / (mig_avg * 1e-3) / 1e12
+    achieved = ops_per_point(w.L) * w.points / (mig_avg * 1e-3) / 1e12
     nparts = b.partials.shape[0]
     line = {
         "metric": "extrapolated points*freq/s (Nx*Nz*Nw/s)", "value": value, "unit": "point*freq/s",
@@ -310,12 +312,12 @@ def run_native(args, w):
                    "mode": "persistent" if args.mode != 2 else "per_depth",
                    "l2": "flushed between steps (256 MiB write)", "partials": nparts,
                    "parallelism": f"{world} independent lines" if world > 1 else "1 line"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s (FP32 pipe)",
+                     "frac": achieved / peak_tops,
                      "traffic": kernel_traffic(w.name) if args.mode != 2 else None,
                      "kernel": "k_migrate_persistent" if args.mode != 2 else "k_migrate_step",
-                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz ({peak_src} max clock)",
-                     "flops_per_point": flops_per_point(w.L), "migrate_ms": mig_avg},
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
+                     "ops_per_point": ops_per_point(w.L), "migrate_ms": mig_avg},
         "e2e": {"value": e2e_val, "unit": "point*freq/s",
                 "h2d_bytes_per_step": int(sec.nbytes + vm.nbytes), "d2h_bytes_per_step": int(d.nz * d.nx * 4),
                 "includes": "H2D section+velocity, t->f, depth loop, imaging, D2H image (table resident)"},
