@@ -211,3 +211,16 @@ def batched_lines(n_lines: int = 64, seed0: int = 1000):
         out.append(Workload(f"line_{i}", nx=nx, dx=12.5, nt=2000, dt=0.002, nz=nz,
                             dz=5.0, f_lo=5.0, f_hi=f_hi, L=L, seed=seed0 + i))
     return out
+
+
+def mlp_init(seed: int = 2, hidden: int = 64, n_out: int = 26) -> "np.ndarray":
+    """Seeded initial parameters of the operator network, flat in the order
+    W1, b1, W2, b2, W3, b3, W4, b4 (each row-major, W[out][in]): weights
+    N(0, 1/fan_in), biases zero.  The draws are inputs shared by the network
+    code and its oracle."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((1, hidden), (hidden, hidden), (hidden, hidden), (hidden, n_out)):
+        parts.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), (fan_out, fan_in)).ravel())
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts)
