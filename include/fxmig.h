@@ -54,6 +54,7 @@ extern "C" {
 /* Workspace kinds for fxmig_workspace_bytes(). */
 #define FXMIG_WS_T2F      1
 #define FXMIG_WS_MIGRATE  2
+#define FXMIG_WS_MLP_MIGRATE 3   /* fxmig_mlp_migrate */
 
 /* Migration forms for fxmig_launch.mode. */
 #define FXMIG_MODE_AUTO       0
@@ -200,6 +201,89 @@ int fxmig_image(const fxmig_desc *d, const float *partials, int nparts, float *i
  * Errors: FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA. */
 int fxmig_migrate_noalloc(const fxmig_desc *d, void *slab, const float *vel, const void *table,
                           float *partials, int nparts, int z_begin, int z_end, void *stream);
+
+
+/* ------------------------------------------------------------------------
+ * Learned operators (extension of Sec. III; the paper designs and stores a
+ * table of operators and picks the nearest entry per point).  A network maps
+ * x = k / k_max, k = w / v, to the L+1 symmetric complex taps of Eq. 1, so the
+ * operator of every point is generated for its exact slowness instead of the
+ * nearest table wavenumber.  Network (hidden width FXMIG_MLP_HIDDEN = 64):
+ *   h1 = gelu(W1 x + b1), h2 = gelu(W2 h1 + b2), h3 = gelu(W3 h2 + b3),
+ *   y = W4 h3 + b4,   y[2n] = Re h_n, y[2n+1] = Im h_n,   gelu(a) = a Phi(a).
+ * Parameters are one float array, each matrix row-major W[out][in], in the
+ * order W1[64][1] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[NO][64] b4[NO],
+ * NO = 2(L+1); L <= 15.  The 64-wide layers run on the tensor cores with
+ * BF16 operands and FP32 accumulation, each operand split into two BF16 terms
+ * (hi + lo, three MMAs per product).  Training minimises the mean squared
+ * error between y and operators of the least-squares design (fxmig_design_at)
+ * with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master parameters.
+ * ------------------------------------------------------------------------ */
+#define FXMIG_MLP_HIDDEN 64
+
+/* Number of network parameters for half-length L, or FXMIG_EINVAL (L > 15). */
+int fxmig_mlp_param_count(int L);
+
+/* Bytes of device workspace of fxmig_mlp_train / fxmig_mlp_grad for n samples
+ * (one partial gradient per 64 samples); 0 for invalid arguments. */
+size_t fxmig_mlp_train_ws_bytes(int L, int n);
+
+/* Least-squares operators (the design of fxmig_design_operators) at n given
+ * wavenumbers instead of the table grid: taps[i] is the operator for k[i].
+ *   k       device, in:  [n] double, 0 <= k
+ *   taps    device, out: [n][L+1] complex64
+ *   taps64  device, out, may be NULL: [n][L+1] complex double
+ * Uses dx, dz, L and theta_max_deg of d.  Errors: FXMIG_EINVAL. */
+int fxmig_design_at(const fxmig_desc *d, const double *k, int n, void *taps, void *taps64, void *stream);
+
+/* nsteps Adam steps of the network on n samples (k[i], taps[i]):
+ * loss = mean over samples and the NO outputs of (y - t)^2, x = k / d->k_max,
+ * t = the taps as NO floats.  Global step numbers step0 .. step0+nsteps-1
+ * (Adam's bias correction uses t = step + 1); learning rate
+ *   lr = lr_min + (lr_max - lr_min) (1 + cos(pi min(step, S) / S)) / 2,  S = schedule_steps,
+ * or lr_max when schedule_steps <= 0.  The gradient is summed over samples
+ * in a fixed order (deterministic).
+ *   params, adam_m, adam_v  device, in/out: [fxmig_mlp_param_count(L)] float
+ *                           (moments start at zero)
+ *   k, taps                 device, in: [n] double, [n][L+1] complex64
+ *   loss                    device, out, may be NULL: [nsteps] float, the loss of
+ *                           each step (before its update)
+ *   ws                      device scratch of fxmig_mlp_train_ws_bytes(L, n) bytes
+ * Errors: FXMIG_EINVAL (invalid d, L > 15, n < 1, k_max <= 0), FXMIG_ENOSPC. */
+int fxmig_mlp_train(const fxmig_desc *d, float *params, float *adam_m, float *adam_v, int step0, int nsteps,
+                    float lr_max, float lr_min, int schedule_steps, const double *k, const void *taps, int n,
+                    float *loss, void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of the training loss with respect to every parameter (same
+ * arithmetic as one fxmig_mlp_train step, no update).
+ *   grad  device, out: [fxmig_mlp_param_count(L)] float
+ *   loss  device, out, may be NULL: [1] float
+ * Errors: as fxmig_mlp_train. */
+int fxmig_mlp_grad(const fxmig_desc *d, const float *params, const double *k, const void *taps, int n,
+                   float *grad, float *loss, void *ws, size_t ws_bytes, void *stream);
+
+/* Network operators at n wavenumbers: taps[i] = network(min(1, max(0, fl32(k[i] / d->k_max)))).
+ *   k     device, in:  [n] double;  taps  device, out: [n][L+1] complex64
+ * Errors: FXMIG_EINVAL. */
+int fxmig_mlp_taps(const fxmig_desc *d, const float *params, const double *k, int n, void *taps, void *stream);
+
+/* Number of partial images fxmig_mlp_migrate writes for d (negative code if
+ * d is invalid for the learned-operator path: L > 15, nx > 16384, k_max <= 0). */
+int fxmig_mlp_num_partials(const fxmig_desc *d);
+
+/* Depth loop of Algorithm 1 over rows [z_begin, z_end) as fxmig_migrate, but
+ * with the operator of point (j, x, z) generated by the network for
+ *   x_in = min(1, max(0, fl32(fl32(w_j / k_max) * s))),  s = fl32(1 / vel[z][x]),
+ * instead of a table entry.  The network runs once per distinct
+ * (frequency, slowness) pair of a velocity row; the wavefield steps stream
+ * through device memory (one launch per depth step).
+ *   slab, vel, partials  as fxmig_migrate; nparts >= fxmig_mlp_num_partials(d)
+ *   params               device, in: trained network (fxmig_mlp_train)
+ *   ws                   device scratch of fxmig_workspace_bytes(d, FXMIG_WS_MLP_MIGRATE)
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA; FXMIG_EVELOCITY via fxmig_check(ws). */
+int fxmig_mlp_migrate(const fxmig_desc *d, void *slab, const float *vel, const float *params,
+                      float *partials, int nparts, int z_begin, int z_end, void *ws, size_t ws_bytes,
+                      void *stream);
 
 /* Waits for `stream`, then reads and returns the device status word in `ws`
  * (FXMIG_OK, FXMIG_EVELOCITY or FXMIG_ETIMEOUT); FXMIG_ECUDA if the stream

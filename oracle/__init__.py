@@ -165,15 +165,13 @@ def response(h: np.ndarray, kx: np.ndarray, dx: float) -> np.ndarray:
     return h @ _basis(np.asarray(kx, dtype=np.float64), dx, h.shape[-1] - 1).T
 
 
-def design_operators(nk: int, k_max: float, dx: float, dz: float, L: int,
-                     theta_deg: float = 65.0, stop_weight: float = 1e-2,
-                     n_samples: int | None = None, guard_points: int = 4096,
-                     return_info: bool = False):
-    """Weighted least-squares design of the operator table (Sec. II, Sec. III).
+def design_at(k, dx: float, dz: float, L: int, theta_deg: float = 65.0, stop_weight: float = 1e-2,
+              n_samples: int | None = None, guard_points: int = 4096, return_info: bool = False):
+    """Weighted least-squares operators (Sec. II, Sec. III) at the wavenumbers k.
 
-    For each k_j = j dk (dk = k_max / (nk-1)) find symmetric taps h[0..L] whose
-    response H(kx) = sum_n c_n h_n cos(n kx dx), c_0 = 1, c_n = 2, fits the
-    one-way downward phase shift
+    For each k find symmetric taps h[0..L] whose response
+    H(kx) = sum_n c_n h_n cos(n kx dx), c_0 = 1, c_n = 2, fits the one-way
+    downward phase shift
         D(kx) = exp(+i sqrt(k^2 - kx^2) dz)   for kx <= k   (propagating)
         D(kx) = exp(-sqrt(kx^2 - k^2) dz)     for kx >  k   (evanescent)
     on M = max(256, 16(L+1)) samples kx_m = m pi / (dx (M-1)), with weight 1
@@ -181,11 +179,11 @@ def design_operators(nk: int, k_max: float, dx: float, dz: float, L: int,
     separately (the basis is real) by Householder QR of sqrt(W) A.  Then the
     amplitude guard: with G = max |H| over ``guard_points`` samples of
     [0, pi/dx], taps are scaled by 1/G when G > 1 (|H| <= 1 keeps the recursion
-    of Eq. 1 stable).  Returns [nk][L+1] complex128 (and a dict of
+    of Eq. 1 stable).  Returns [len(k)][L+1] complex128 (and a dict of
     intermediates when ``return_info``).
     """
+    k = np.atleast_1d(np.asarray(k, dtype=np.float64))
     M = n_samples or max(256, 16 * (L + 1))
-    k, dk = k_grid(nk, k_max)
     kx = np.arange(M, dtype=np.float64) * (math.pi / (dx * (M - 1)))
     A = _basis(kx, dx, L)                                      # [M][L+1]
     kz2 = k[:, None] ** 2 - kx[None, :] ** 2                   # [nk][M]
@@ -203,9 +201,23 @@ def design_operators(nk: int, k_max: float, dx: float, dz: float, L: int,
     scale = np.where(G > 1.0, 1.0 / G, 1.0)
     h = h_ls * scale[:, None]
     if return_info:
-        return h, {"k": k, "dk": dk, "kx": kx, "A": A, "D": D, "W": W, "h_ls": h_ls,
-                   "G": G, "scale": scale, "kx_guard": kxd}
+        return h, {"k": k, "kx": kx, "A": A, "D": D, "W": W, "h_ls": h_ls, "G": G, "scale": scale,
+                   "kx_guard": kxd}
     return h
+
+
+def design_operators(nk: int, k_max: float, dx: float, dz: float, L: int,
+                     theta_deg: float = 65.0, stop_weight: float = 1e-2,
+                     n_samples: int | None = None, guard_points: int = 4096,
+                     return_info: bool = False):
+    """The operator table of Sec. III: ``design_at`` on the grid k_j = j dk,
+    dk = k_max / (nk - 1).  Returns [nk][L+1] complex128 (and the
+    intermediates, with "dk", when ``return_info``)."""
+    k, dk = k_grid(nk, k_max)
+    out = design_at(k, dx, dz, L, theta_deg, stop_weight, n_samples, guard_points, return_info)
+    if return_info:
+        out[1]["dk"] = dk
+    return out
 
 
 # ------------------------------------------------------------ lookup and steps
@@ -299,3 +311,68 @@ def model(refl: np.ndarray, vel: np.ndarray, table: np.ndarray, q: np.ndarray,
     if rc != 0:
         raise MemoryError("oracle model: allocation failed")
     return out
+
+
+# ------------------------------------------------- pointwise operators (no table)
+def convolve_pointwise(P: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """Eq. 1 with its own operator at every output point:
+    out[j][x] = h[j][x][0] P[j][x] + sum_{n=1}^{L} h[j][x][n] (P[j][x-n] + P[j][x+n]),
+    P = 0 outside [0, nx).  P [nw][nx], h [nw][nx][L+1]; FP64."""
+    P = np.asarray(P, dtype=np.complex128)
+    h = np.asarray(h, dtype=np.complex128)
+    nx = P.shape[1]
+    L = h.shape[2] - 1
+    Pp = np.pad(P, ((0, 0), (L, L)))
+    out = h[:, :, 0] * P
+    for n in range(1, L + 1):
+        out = out + h[:, :, n] * (Pp[:, L - n:L - n + nx] + Pp[:, L + n:L + n + nx])
+    return out
+
+
+def migrate_pointwise(P0: np.ndarray, vel: np.ndarray, w: np.ndarray, taps_fn,
+                      z_begin: int = 0, z_end: int | None = None):
+    """Algorithm 1's depth loop with the operator of point (j, x, z) produced by
+    ``taps_fn(w_pairs, s_pairs) -> [n][L+1]`` for frequency w_j and slowness
+    s = fl32(1 / vel[z][x]) instead of a table row.  The function is called
+    once per row on the distinct (w, s) pairs of that row.  Returns (P at
+    depth z_end, image [nz][nx]) like ``migrate``; FP64 arithmetic."""
+    P = np.asarray(P0, dtype=np.complex128).copy()
+    vel = np.asarray(vel, dtype=np.float32)
+    nz, nx = vel.shape
+    w = np.asarray(w, dtype=np.float64)
+    z_end = nz if z_end is None else z_end
+    image = np.zeros((nz, nx), dtype=np.float64)
+    for z in range(z_begin, z_end):
+        image[z] = P.real.sum(axis=0)
+        s = slowness(vel[z])
+        su, inv = np.unique(s, return_inverse=True)
+        h = np.asarray(taps_fn(np.repeat(w, su.size), np.tile(su, w.size)))   # pairs (w_j, su_u), j-major
+        L1 = h.shape[1]
+        hp = h.reshape(w.size, su.size, L1)[:, inv.ravel(), :]                  # [nw][nx][L+1]
+        P = convolve_pointwise(P, hp)
+    return P, image
+
+
+def table_taps_fn(table: np.ndarray, q: np.ndarray, w: np.ndarray):
+    """The table lookup of Sec. III as a ``taps_fn``: the row
+    rint_half_even(fl32(q_j s)) clamped, q_j the table factor of frequency w_j."""
+    table = np.asarray(table)
+    w = np.asarray(w, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float32)
+
+    def fn(wp, sp):
+        j = np.searchsorted(w, wp)
+        qs = (q[j] * np.asarray(sp, dtype=np.float32)).astype(np.float32)
+        return table[np.clip(np.rint(qs).astype(np.int64), 0, table.shape[0] - 1)]
+    return fn
+
+
+def design_taps_fn(dx: float, dz: float, L: int, theta_deg: float = 65.0):
+    """Least-squares operators designed at the exact wavenumber k = w s of every
+    point (``design_at``): the continuous-velocity reference, free of table
+    quantisation."""
+    def fn(wp, sp):
+        k = np.asarray(wp, dtype=np.float64) * np.asarray(sp, dtype=np.float32).astype(np.float64)
+        ku, inv = np.unique(k, return_inverse=True)
+        return design_at(ku, dx, dz, L, theta_deg)[inv.ravel()]
+    return fn

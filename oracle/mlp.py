@@ -97,3 +97,22 @@ def adam_step(v: np.ndarray, grad: np.ndarray, m: np.ndarray, s: np.ndarray, ste
 def taps_from_output(y: np.ndarray) -> np.ndarray:
     """[n][2(L+1)] interleaved (Re, Im) -> [n][L+1] complex taps."""
     return y[:, 0::2] + 1j * y[:, 1::2]
+
+
+def taps_at(v: np.ndarray, k, k_max: float, L: int, hidden: int = 64) -> np.ndarray:
+    """Operators generated by the network with flat parameters v at the
+    wavenumbers k: input x = k / k_max clipped to [0, 1] (the domain the
+    network is trained on); [n][L+1] complex128."""
+    x = np.clip(np.asarray(k, dtype=np.float64) / k_max, 0.0, 1.0)
+    y, _ = forward(unflatten(v, hidden, 2 * (L + 1)), x)
+    return taps_from_output(y)
+
+
+def taps_fn(v: np.ndarray, k_max: float, L: int, hidden: int = 64):
+    """``taps_at`` as the operator generator of ``oracle.migrate_pointwise``
+    (pairs of frequency w and slowness s, k = w s)."""
+    def fn(wp, sp):
+        k = np.asarray(wp, dtype=np.float64) * np.asarray(sp, dtype=np.float32).astype(np.float64)
+        ku, inv = np.unique(k, return_inverse=True)
+        return taps_at(v, ku, k_max, L, hidden)[inv.ravel()]
+    return fn

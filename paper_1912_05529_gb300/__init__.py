@@ -21,15 +21,17 @@ import os
 
 __all__ = [
     "FXMIG_OK", "FXMIG_EINVAL", "FXMIG_ENOSPC", "FXMIG_ECUDA", "FXMIG_ETIMEOUT", "FXMIG_EVELOCITY",
-    "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
+    "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_WS_MLP_MIGRATE", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
     "FxmigError", "Desc", "Launch", "lib", "library_path",
     "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
     "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
     "fxmig_check", "fxmig_migrate_noalloc", "desc_for", "migrate_section",
+    "fxmig_mlp_param_count", "fxmig_mlp_train_ws_bytes", "fxmig_design_at", "fxmig_mlp_train",
+    "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials", "fxmig_mlp_migrate",
 ]
 
 FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
-FXMIG_WS_T2F, FXMIG_WS_MIGRATE = 1, 2
+FXMIG_WS_T2F, FXMIG_WS_MIGRATE, FXMIG_WS_MLP_MIGRATE = 1, 2, 3
 FXMIG_MODE_AUTO, FXMIG_MODE_PERSISTENT, FXMIG_MODE_PER_DEPTH = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -87,8 +89,20 @@ def lib():
         L.fxmig_migrate_ex.argtypes = [pd, pl, vp, vp, vp, vp, i, i, i, vp, sz, vp]
         L.fxmig_image.argtypes = [pd, vp, i, vp, vp]
         L.fxmig_check.argtypes = [vp, vp]
+        fl = ctypes.c_float
+        L.fxmig_mlp_param_count.argtypes = [i]
+        L.fxmig_mlp_train_ws_bytes.argtypes = [i, i]
+        L.fxmig_mlp_train_ws_bytes.restype = sz
+        L.fxmig_design_at.argtypes = [pd, vp, i, vp, vp, vp]
+        L.fxmig_mlp_train.argtypes = [pd, vp, vp, vp, i, i, fl, fl, i, vp, vp, i, vp, vp, sz, vp]
+        L.fxmig_mlp_grad.argtypes = [pd, vp, vp, vp, i, vp, vp, vp, sz, vp]
+        L.fxmig_mlp_taps.argtypes = [pd, vp, vp, i, vp, vp]
+        L.fxmig_mlp_num_partials.argtypes = [pd]
+        L.fxmig_mlp_migrate.argtypes = [pd, vp, vp, vp, vp, i, i, i, vp, sz, vp]
         for f in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex",
-                  "fxmig_image", "fxmig_check"):
+                  "fxmig_image", "fxmig_check", "fxmig_mlp_param_count", "fxmig_design_at",
+                  "fxmig_mlp_train", "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials",
+                  "fxmig_mlp_migrate"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -223,6 +237,96 @@ def fxmig_migrate_noalloc(d: Desc, slab, vel, table, partials, z_begin, z_end, s
     nparts = partials.numel() // max(1, d.nz * d.nx)
     _check(f(ctypes.byref(d), bp, vp, tp, pp, int(nparts), int(z_begin), int(z_end), _stream(stream)),
            "fxmig_migrate_noalloc")
+
+
+# ------------------------------------------------------------ learned operators
+def fxmig_mlp_param_count(L: int) -> int:
+    n = lib().fxmig_mlp_param_count(int(L))
+    if n < 0:
+        raise FxmigError(n, "fxmig_mlp_param_count")
+    return n
+
+
+def fxmig_mlp_train_ws_bytes(L: int, n: int) -> int:
+    return int(lib().fxmig_mlp_train_ws_bytes(int(L), int(n)))
+
+
+def _taps_ptr(taps, what, n, L):
+    torch = _torch()
+    return _dev_ptr(taps, what, torch.float32, 2 * n * (L + 1), complex_ok=True)
+
+
+def fxmig_design_at(d: Desc, k, taps, taps64=None, stream=None) -> None:
+    """k: [n] float64 (device); taps: [n][L+1] complex64; taps64: complex128 or None."""
+    torch = _torch()
+    n = k.numel()
+    kp = _dev_ptr(k, "k", torch.float64)
+    tp = _taps_ptr(taps, "taps", n, d.L)
+    t64 = None
+    if taps64 is not None:
+        if taps64.dtype not in (torch.complex128, torch.float64):
+            raise TypeError("taps64: expected complex128 or float64")
+        t64 = _dev_ptr(taps64, "taps64", None, 2 * n * (d.L + 1))
+    _check(lib().fxmig_design_at(ctypes.byref(d), kp, int(n), tp, t64, _stream(stream)), "fxmig_design_at")
+
+
+def fxmig_mlp_train(d: Desc, params, adam_m, adam_v, step0, nsteps, lr_max, lr_min, schedule_steps, k, taps,
+                    ws, loss=None, stream=None) -> None:
+    """nsteps Adam steps on samples (k[i], taps[i]); loss: [nsteps] float32 or None."""
+    torch = _torch()
+    P = fxmig_mlp_param_count(d.L)
+    n = k.numel()
+    lp = _dev_ptr(loss, "loss", torch.float32, int(nsteps)) if loss is not None else None
+    rc = lib().fxmig_mlp_train(ctypes.byref(d), _dev_ptr(params, "params", torch.float32, P),
+                               _dev_ptr(adam_m, "adam_m", torch.float32, P),
+                               _dev_ptr(adam_v, "adam_v", torch.float32, P), int(step0), int(nsteps),
+                               float(lr_max), float(lr_min), int(schedule_steps), _dev_ptr(k, "k", torch.float64),
+                               _taps_ptr(taps, "taps", n, d.L), int(n), lp, _dev_ptr(ws, "ws"),
+                               ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "fxmig_mlp_train")
+
+
+def fxmig_mlp_grad(d: Desc, params, k, taps, grad, ws, loss=None, stream=None) -> None:
+    torch = _torch()
+    P = fxmig_mlp_param_count(d.L)
+    n = k.numel()
+    lp = _dev_ptr(loss, "loss", torch.float32, 1) if loss is not None else None
+    rc = lib().fxmig_mlp_grad(ctypes.byref(d), _dev_ptr(params, "params", torch.float32, P),
+                              _dev_ptr(k, "k", torch.float64), _taps_ptr(taps, "taps", n, d.L), int(n),
+                              _dev_ptr(grad, "grad", torch.float32, P), lp, _dev_ptr(ws, "ws"),
+                              ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "fxmig_mlp_grad")
+
+
+def fxmig_mlp_taps(d: Desc, params, k, taps, stream=None) -> None:
+    torch = _torch()
+    n = k.numel()
+    rc = lib().fxmig_mlp_taps(ctypes.byref(d), _dev_ptr(params, "params", torch.float32,
+                                                        fxmig_mlp_param_count(d.L)),
+                              _dev_ptr(k, "k", torch.float64), int(n), _taps_ptr(taps, "taps", n, d.L),
+                              _stream(stream))
+    _check(rc, "fxmig_mlp_taps")
+
+
+def fxmig_mlp_num_partials(d: Desc) -> int:
+    n = lib().fxmig_mlp_num_partials(ctypes.byref(d))
+    if n < 0:
+        raise FxmigError(n, "fxmig_mlp_num_partials")
+    return n
+
+
+def fxmig_mlp_migrate(d: Desc, slab, vel, params, partials, z_begin, z_end, ws, stream=None) -> None:
+    """Depth loop with network operators at the exact slowness of every point."""
+    torch = _torch()
+    bp = _dev_ptr(slab, "slab", torch.float32, 2 * d.nw * d.nx, complex_ok=True)
+    vp = _dev_ptr(vel, "vel", torch.float32, d.nz * d.nx)
+    mp = _dev_ptr(params, "params", torch.float32, fxmig_mlp_param_count(d.L))
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * d.nx)
+    wp = _dev_ptr(ws, "ws")
+    rc = lib().fxmig_mlp_migrate(ctypes.byref(d), bp, vp, mp, pp, int(nparts), int(z_begin), int(z_end), wp,
+                                 ws.numel() * ws.element_size(), _stream(stream))
+    _check(rc, "fxmig_mlp_migrate")
 
 
 # ------------------------------------------------------------------ conveniences

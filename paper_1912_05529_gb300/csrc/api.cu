@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "fxmig_internal.cuh"
+#include "mlp_internal.cuh"
 
 using namespace fxmig_impl;
 
@@ -59,6 +60,7 @@ size_t fxmig_workspace_bytes(const fxmig_desc* d, int kind) {
     if (!desc_valid(d)) return 0;
     if (kind == FXMIG_WS_T2F) return t2f_ws_bytes(d);
     if (kind == FXMIG_WS_MIGRATE) return migrate_ws_bytes(d);
+    if (kind == FXMIG_WS_MLP_MIGRATE) return mlp_migrate_ws_bytes(d);
     return 0;
 }
 
@@ -71,7 +73,7 @@ int fxmig_num_partials(const fxmig_desc* d, const fxmig_launch* launch) {
 
 int fxmig_design_operators(const fxmig_desc* d, void* table, void* table64, void* stream) {
     if (!desc_valid(d) || !table || !aligned(table, 8) || (table64 && !aligned(table64, 16))) return FXMIG_EINVAL;
-    const cudaError_t e = launch_design(d, table, table64, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_design(d, nullptr, d->nk, table, table64, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_design_operators");
 }
 
@@ -114,6 +116,88 @@ int fxmig_image(const fxmig_desc* d, const float* partials, int nparts, float* i
     if (!aligned(partials, 4) || !aligned(image, 4)) return FXMIG_EINVAL;
     const cudaError_t e = launch_image(d, partials, nparts, image, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_image");
+}
+
+int fxmig_mlp_param_count(int L) {
+    if (L < 0 || L > kMlpMaxL) return FXMIG_EINVAL;
+    return mlp_param_count(L);
+}
+
+size_t fxmig_mlp_train_ws_bytes(int L, int n) {
+    if (L < 0 || L > kMlpMaxL || n < 1) return 0;
+    return mlp_train_ws_bytes(L, n);
+}
+
+int fxmig_design_at(const fxmig_desc* d, const double* k, int n, void* taps, void* taps64, void* stream) {
+    if (!desc_valid(d) || n < 0 || (n > 0 && (!k || !taps))) return FXMIG_EINVAL;
+    if ((k && !aligned(k, 8)) || (taps && !aligned(taps, 8)) || (taps64 && !aligned(taps64, 16))) return FXMIG_EINVAL;
+    const cudaError_t e = launch_design(d, k, n, taps, taps64, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_design_at");
+}
+
+static int mlp_train_args_ok(const fxmig_desc* d, const double* k, const void* taps, int n, void* ws) {
+    if (!desc_valid(d) || d->L > kMlpMaxL || !(d->k_max > 0) || n < 1 || !k || !taps || !ws) return FXMIG_EINVAL;
+    if (!aligned(k, 8) || !aligned(taps, 8) || !aligned(ws, 256)) return FXMIG_EINVAL;
+    return FXMIG_OK;
+}
+
+int fxmig_mlp_train(const fxmig_desc* d, float* params, float* adam_m, float* adam_v, int step0, int nsteps,
+                    float lr_max, float lr_min, int schedule_steps, const double* k, const void* taps, int n,
+                    float* loss, void* ws, size_t ws_bytes, void* stream) {
+    int rc = mlp_train_args_ok(d, k, taps, n, ws);
+    if (rc != FXMIG_OK) return rc;
+    if (!params || !adam_m || !adam_v || step0 < 0 || nsteps < 0 || !(lr_max >= 0) || !(lr_min >= 0))
+        return FXMIG_EINVAL;
+    if (!aligned(params, 4) || !aligned(adam_m, 4) || !aligned(adam_v, 4) || (loss && !aligned(loss, 4)))
+        return FXMIG_EINVAL;
+    if (ws_bytes < mlp_train_ws_bytes(d->L, n)) return FXMIG_ENOSPC;
+    const cudaError_t e = launch_mlp_train(d->L, params, adam_m, adam_v, step0, nsteps, lr_max, lr_min,
+                                           schedule_steps, k, d->k_max, static_cast<const float*>(taps), n, loss,
+                                           nullptr, ws, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_mlp_train");
+}
+
+int fxmig_mlp_grad(const fxmig_desc* d, const float* params, const double* k, const void* taps, int n,
+                   float* grad, float* loss, void* ws, size_t ws_bytes, void* stream) {
+    int rc = mlp_train_args_ok(d, k, taps, n, ws);
+    if (rc != FXMIG_OK) return rc;
+    if (!params || !grad || !aligned(params, 4) || !aligned(grad, 4) || (loss && !aligned(loss, 4)))
+        return FXMIG_EINVAL;
+    if (ws_bytes < mlp_train_ws_bytes(d->L, n)) return FXMIG_ENOSPC;
+    // the gradient-only step reads the parameters and writes grad, never params
+    const cudaError_t e = launch_mlp_train(d->L, const_cast<float*>(params), nullptr, nullptr, 0, 1, 0.f, 0.f, 0, k,
+                                           d->k_max, static_cast<const float*>(taps), n, loss, grad, ws,
+                                           static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_mlp_grad");
+}
+
+int fxmig_mlp_taps(const fxmig_desc* d, const float* params, const double* k, int n, void* taps, void* stream) {
+    if (!desc_valid(d) || d->L > kMlpMaxL || !(d->k_max > 0) || !params || n < 0) return FXMIG_EINVAL;
+    if (n > 0 && (!k || !taps || !aligned(k, 8) || !aligned(taps, 8))) return FXMIG_EINVAL;
+    const cudaError_t e = launch_mlp_taps(d->L, params, k, d->k_max, n, taps, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_mlp_taps");
+}
+
+int fxmig_mlp_num_partials(const fxmig_desc* d) {
+    if (!desc_valid(d)) return FXMIG_EINVAL;
+    MlpMigratePlan p;
+    const int rc = plan_mlp_migrate(d, &p);
+    return rc == FXMIG_OK ? p.nparts : rc;
+}
+
+int fxmig_mlp_migrate(const fxmig_desc* d, void* slab, const float* vel, const float* params, float* partials,
+                      int nparts, int z_begin, int z_end, void* ws, size_t ws_bytes, void* stream) {
+    if (!desc_valid(d) || !slab || !vel || !params || !partials || !ws) return FXMIG_EINVAL;
+    if (!aligned(slab, 8) || !aligned(vel, 4) || !aligned(params, 4) || !aligned(partials, 4) || !aligned(ws, 256))
+        return FXMIG_EINVAL;
+    if (z_begin < 0 || z_end < z_begin || z_end > d->nz) return FXMIG_EINVAL;
+    MlpMigratePlan plan;
+    const int rc = plan_mlp_migrate(d, &plan);
+    if (rc != FXMIG_OK) return rc;
+    if (nparts < plan.nparts || ws_bytes < mlp_migrate_ws_bytes(d)) return FXMIG_ENOSPC;
+    const cudaError_t e = launch_mlp_migrate(d, plan, slab, vel, params, partials, z_begin, z_end, ws,
+                                             static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_mlp_migrate");
 }
 
 int fxmig_check(const void* ws, void* stream) {

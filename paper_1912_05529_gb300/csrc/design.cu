@@ -20,8 +20,10 @@ namespace fxmig_impl {
 
 constexpr int kGuardPoints = 4096;
 
-__global__ void __launch_bounds__(256) k_design(int nk, double dk, double dx, double dz, int L,
-                                                 double sin_theta, int M, float2* table, double2* table64) {
+// kvals == nullptr: the table grid k_j = j dk; else the wavenumbers kvals[j].
+__global__ void __launch_bounds__(256) k_design(int nk, double dk, const double* __restrict__ kvals, double dx,
+                                                 double dz, int L, double sin_theta, int M, float2* table,
+                                                 double2* table64) {
     extern __shared__ __align__(16) double sd[];
     const int n1 = L + 1;
     double* A = sd;                    // [M][n1]
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(256) k_design(int nk, double dk, double dx, do
     double* bi = br + n1;              // [n1]
     double* red = bi + n1;             // [256]
     const int j = blockIdx.x, tid = threadIdx.x;
-    const double k = (double)j * dk;
+    const double k = kvals ? kvals[j] : (double)j * dk;
     const double cdx = 3.14159265358979323846 / (dx * (double)(M - 1));
     const double ks = k * sin_theta;
     for (int m = tid; m < M; m += blockDim.x) {
@@ -122,7 +124,8 @@ __global__ void __launch_bounds__(256) k_design(int nk, double dk, double dx, do
     }
 }
 
-cudaError_t launch_design(const fxmig_desc* d, void* table, void* table64, cudaStream_t s) {
+cudaError_t launch_design(const fxmig_desc* d, const double* kvals, int n, void* table, void* table64,
+                          cudaStream_t s) {
     const int n1 = d->L + 1;
     const int M = n1 * 16 > 256 ? n1 * 16 : 256;
     const double dk = d->nk > 1 ? d->k_max / (double)(d->nk - 1) : 0.0;
@@ -130,8 +133,9 @@ cudaError_t launch_design(const fxmig_desc* d, void* table, void* table64, cudaS
     const size_t smem = ((size_t)M * n1 + 3 * (size_t)M + (size_t)n1 * n1 + 2 * (size_t)n1 + 256) * 8;
     cudaError_t e = cudaFuncSetAttribute(k_design, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_design<<<d->nk, 256, smem, s>>>(d->nk, dk, d->dx, d->dz, d->L, sin_theta, M, static_cast<float2*>(table),
-                                       static_cast<double2*>(table64));
+    if (n == 0) return cudaSuccess;
+    k_design<<<n, 256, smem, s>>>(n, dk, kvals, d->dx, d->dz, d->L, sin_theta, M, static_cast<float2*>(table),
+                                  static_cast<double2*>(table64));
     return cudaGetLastError();
 }
 

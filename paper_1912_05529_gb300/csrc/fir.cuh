@@ -23,14 +23,15 @@ __device__ __forceinline__ int table_index(float q, float s, int nk) {
     return min(max(idx, 0), nk - 1);
 }
 
-// Eq. 1 for 8 consecutive outputs.  wbase points at the padded position of
-// the first window value (x of the first output minus L).  Outputs are
+// Eq. 1 for 8 consecutive outputs, output r with its own taps tp[r]
+// ([LT+1] of (hr, hr, hi, hi)).  wbase points at the padded position of the
+// first window value (x of the first output minus L).  Outputs are
 //   out_r = h0 P_r + sum_{n=1}^{L} h_n (P_{r-n} + P_{r+n}),
 // accumulated as A = sum hr * (pair) and B = sum hi * (pair) with packed
 // (re, im) f32x2 operations, then out = (A.re - B.im, A.im + B.re).
 template <int LT>
-__device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const float (&s8)[8], float q, int nk,
-                                     const float4* __restrict__ taps, u64 (&res)[8], float (&re)[8]) {
+__device__ __forceinline__ void fir8_ptrs(const float2* __restrict__ wbase, const float4* const (&tp)[8],
+                                          u64 (&res)[8], float (&re)[8]) {
     constexpr int NWIN = 8 + 2 * LT;
     u64 w[NWIN];
 #pragma unroll
@@ -41,9 +42,6 @@ __device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const flo
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) re[r] = f2_unpack(w[LT + r]).x;
-    const float4* tp[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) tp[r] = taps + (size_t)table_index(q, s8[r], nk) * (LT + 1);
     u64 A[8], B[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -68,6 +66,17 @@ __device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const flo
         const float2 a = f2_unpack(A[r]), b = f2_unpack(B[r]);
         res[r] = f2_pack(a.x - b.y, a.y + b.x);
     }
+}
+
+// Eq. 1 for 8 consecutive outputs with the table operators of Sec. III:
+// output r uses table row table_index(q, s8[r]).
+template <int LT>
+__device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const float (&s8)[8], float q, int nk,
+                                     const float4* __restrict__ taps, u64 (&res)[8], float (&re)[8]) {
+    const float4* tp[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) tp[r] = taps + (size_t)table_index(q, s8[r], nk) * (LT + 1);
+    fir8_ptrs<LT>(wbase, tp, res, re);
 }
 
 // Store 8 outputs at padded positions LT + r relative to the 8-aligned base.

@@ -182,7 +182,9 @@ size_t migrate_ws_bytes(const fxmig_desc* d);
 size_t t2f_ws_bytes(const fxmig_desc* d);
 bool t2f_supported(int nt);
 
-cudaError_t launch_design(const fxmig_desc* d, void* table, void* table64, cudaStream_t s);
+// kvals == nullptr: the nk-entry table grid (n == nk); else n wavenumbers kvals.
+cudaError_t launch_design(const fxmig_desc* d, const double* kvals, int n, void* table, void* table64,
+                          cudaStream_t s);
 cudaError_t launch_t2f(const fxmig_desc* d, const float* section, void* slab, void* ws, cudaStream_t s);
 // precompute_slowness: write fl32(1/vel) into the workspace first and stage
 // slowness rows (needs the full FXMIG_WS_MIGRATE workspace); false: convert

@@ -1,0 +1,57 @@
+"""Pins of the pointwise-operator oracle (operators generated per point, no
+table): brute-force banded matrices, agreement with the table oracle when the
+generator is the table lookup of Sec. III, and the network generator's input
+clipping."""
+import numpy as np
+
+import oracle as O
+import workloads as W
+from oracle import mlp
+
+
+def test_convolve_pointwise_is_banded_matrix_product():
+    rng = np.random.default_rng(1)
+    nw, nx, L = 3, 23, 4
+    P = rng.normal(size=(nw, nx)) + 1j * rng.normal(size=(nw, nx))
+    h = rng.normal(size=(nw, nx, L + 1)) + 1j * rng.normal(size=(nw, nx, L + 1))
+    out = O.convolve_pointwise(P, h)
+    for j in range(nw):
+        M = np.zeros((nx, nx), dtype=np.complex128)
+        for x in range(nx):
+            for xp in range(max(0, x - L), min(nx, x + L + 1)):
+                M[x, xp] = h[j, x, abs(x - xp)]
+        assert np.allclose(out[j], M @ P[j], rtol=0, atol=1e-12)
+
+
+def test_pointwise_with_table_lookup_equals_table_oracle(oracle_mod):
+    wl = W.Workload("t", nx=61, dx=12.5, nt=128, dt=0.004, nz=12, dz=5.0, f_lo=5, f_hi=60, L=6, seed=5)
+    v, refl = W.layered_lens_model(wl)
+    sec = W.normal_incidence_section(wl, v, refl)
+    vm = (v / 2).astype(np.float32)
+    P0 = O.band_dft(sec, wl.i0, wl.nw)
+    w = O.omegas(wl.i0, wl.nw, wl.nt, wl.dt)
+    k_max = w.max() / float(vm.min())
+    table = O.design_operators(wl.nk, k_max, wl.dx, wl.dz, wl.L)
+    _, dk = O.k_grid(wl.nk, k_max)
+    q = O.q_values(w, dk)
+    P_c, img_c = O.migrate(P0, vm, table, q)
+    P_p, img_p = O.migrate_pointwise(P0, vm, w, O.table_taps_fn(table, q, w))
+    assert np.abs(P_p - P_c).max() <= 1e-13 * np.abs(P_c).max()
+    assert np.abs(img_p - img_c).max() <= 1e-13 * np.abs(img_c).max()
+
+
+def test_design_taps_fn_matches_design_at_on_grid():
+    # on table wavenumbers the pointwise design is the table row
+    k_max, nk = 0.3, 64
+    table = O.design_operators(nk, k_max, 12.5, 5.0, 5)
+    k, _ = O.k_grid(nk, k_max)
+    sel = np.array([0, 7, 31, 63])
+    h = O.design_at(k[sel], 12.5, 5.0, 5)
+    assert np.array_equal(h, table[sel])
+
+
+def test_network_input_is_clipped_to_unit_interval():
+    v = W.mlp_init(4, n_out=12)
+    k_max = 0.5
+    t = mlp.taps_at(v, np.array([-0.1, 0.0, 0.5, 0.6]), k_max, 5)
+    assert np.array_equal(t[0], t[1]) and np.array_equal(t[2], t[3])

@@ -213,14 +213,18 @@ def batched_lines(n_lines: int = 64, seed0: int = 1000):
     return out
 
 
-def mlp_init(seed: int = 2, hidden: int = 64, n_out: int = 26) -> "np.ndarray":
+def mlp_init(seed: int = 2, hidden: int = 64, n_out: int = 26, input_scale: float = 8.0) -> "np.ndarray":
     """Seeded initial parameters of the operator network, flat in the order
-    W1, b1, W2, b2, W3, b3, W4, b4 (each row-major, W[out][in]): weights
-    N(0, 1/fan_in), biases zero.  The draws are inputs shared by the network
-    code and its oracle."""
+    W1, b1, W2, b2, W3, b3, W4, b4 (each row-major, W[out][in]).  The scalar
+    input lies in [0, 1]: W1 ~ N(0, input_scale^2) and b1 = -W1 c with
+    c ~ U(0, 1), so the first-layer units bend at points spread over the
+    input range; the other weights are N(0, 1/fan_in) and their biases zero.
+    The draws are inputs shared by the network code and its oracle."""
     rng = np.random.default_rng(seed)
-    parts = []
-    for fan_in, fan_out in ((1, hidden), (hidden, hidden), (hidden, hidden), (hidden, n_out)):
+    W1 = rng.normal(0.0, input_scale, (hidden, 1))
+    b1 = -W1[:, 0] * rng.uniform(0.0, 1.0, hidden)
+    parts = [W1.ravel(), b1]
+    for fan_in, fan_out in ((hidden, hidden), (hidden, hidden), (hidden, n_out)):
         parts.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), (fan_out, fan_in)).ravel())
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts)
