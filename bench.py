@@ -120,6 +120,12 @@ def k_max_of(w: W.Workload, vm_min: float) -> float:
     return 2.0 * math.pi * (w.i0 + w.nw - 1) / (w.nt * w.dt) / vm_min
 
 
+# sources of the persistent depth-loop kernel (the traffic record is valid
+# only for the exact sources it was captured from)
+KERNEL_SOURCES = ("paper_1912_05529_gb300/csrc/migrate.cu", "paper_1912_05529_gb300/csrc/persistent.cuh",
+                  "paper_1912_05529_gb300/csrc/fir.cuh", "paper_1912_05529_gb300/csrc/fxmig_internal.cuh")
+
+
 def kernel_traffic(workload: str):
     """DRAM bytes per launch of the persistent depth-loop kernel from the ncu
     capture recorded under profiles/, or None if the kernel sources changed
@@ -132,8 +138,7 @@ def kernel_traffic(workload: str):
     except (OSError, ValueError):
         return None
     h = hashlib.sha256()
-    for rel in ("paper_1912_05529_gb300/csrc/migrate.cu", "paper_1912_05529_gb300/csrc/fir.cuh",
-                "paper_1912_05529_gb300/csrc/fxmig_internal.cuh"):
+    for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return rec.get("dram_bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
@@ -202,6 +207,92 @@ def run_reference(args, w):
             "e2e": {"value": val, "unit": "point*freq/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_learned(fx, d, b, slab0, steps, flush, train_steps=100000, n_train=8192, seed=2):
+    """The learned-operator form on the same inputs: train the operator network
+    on the GPU (n_train designed operators at k ~ U[0, k_max], seeded), then
+    time fxmig_mlp_migrate + fxmig_image like the plain form."""
+    import torch
+    k = torch.from_numpy(np.random.default_rng(seed).uniform(0.0, d.k_max, n_train)).cuda()
+    taps = torch.empty((n_train, d.L + 1), dtype=torch.complex64, device="cuda")
+    P = fx.fxmig_mlp_param_count(d.L)
+    params = torch.from_numpy(W.mlp_init(seed, n_out=2 * (d.L + 1)).astype(np.float32)).cuda()
+    m = torch.zeros(P, device="cuda")
+    v = torch.zeros(P, device="cuda")
+    ws_t = torch.empty(fx.fxmig_mlp_train_ws_bytes(d.L, n_train), dtype=torch.uint8, device="cuda")
+    loss = torch.empty(train_steps, device="cuda")
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    fx.fxmig_design_at(d, k, taps)
+    fx.fxmig_mlp_train(d, params, m, v, 0, train_steps, 3e-3, 1e-5, train_steps, k, taps, ws_t, loss=loss)
+    t1.record()
+    torch.cuda.synchronize()
+    train_ms = t0.elapsed_time(t1)
+    nparts = fx.fxmig_mlp_num_partials(d)
+    partials = torch.zeros((nparts, d.nz, d.nx), dtype=torch.float32, device="cuda")
+    ws = torch.empty(fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MLP_MIGRATE), dtype=torch.uint8, device="cuda")
+    image = torch.empty((d.nz, d.nx), dtype=torch.float32, device="cuda")
+    slab = torch.empty_like(slab0)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        slab.copy_(slab0)
+        fx.fxmig_mlp_migrate(d, slab, b.vel, params, partials, 0, d.nz, ws)
+        fx.fxmig_image(d, partials, image)
+    torch.cuda.synchronize()
+    if fx.fxmig_check(ws) != fx.FXMIG_OK:
+        raise RuntimeError("learned form: device status " + fx.fxmig_strerror(fx.fxmig_check(ws)))
+    ms = []
+    for _ in range(steps):
+        slab.copy_(slab0)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fx.fxmig_mlp_migrate(d, slab, b.vel, params, partials, 0, d.nz, ws)
+        fx.fxmig_image(d, partials, image)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    l = loss.cpu().numpy()
+    return {"ms_per_step": float(np.mean(ms)), "train_ms": train_ms, "train_steps": train_steps,
+            "train_samples": n_train, "train_loss_first_last": [float(l[0]), float(l[-1])],
+            "image": image.cpu().numpy()}
+
+
+PREC_NAMES = ("FP16_SPLIT", "BF16_SPLIT", "FP16", "BF16")
+
+
+def measure_precision(fx, d, b, slab0, steps, flush, launch, prec):
+    """A 16-bit storage form of the persistent depth loop on the same inputs:
+    mean CUDA-event time of fxmig_migrate_ex + fxmig_image, and its image."""
+    import torch
+    lc = fx.Launch(mode=fx.FXMIG_MODE_PERSISTENT, cluster=launch.cluster, groups=launch.groups,
+                   warps=launch.warps, precision=prec)
+    nparts = fx.fxmig_num_partials(d, lc)
+    partials = torch.zeros((nparts, d.nz, d.nx), dtype=torch.float32, device="cuda")
+    image = torch.empty((d.nz, d.nx), dtype=torch.float32, device="cuda")
+    slab = torch.empty_like(slab0)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        slab.copy_(slab0)
+        fx.fxmig_migrate_ex(d, lc, slab, b.vel, b.table, partials, 0, d.nz, b.ws_mig)
+        fx.fxmig_image(d, partials, image)
+    torch.cuda.synchronize()
+    if fx.fxmig_check(b.ws_mig) != fx.FXMIG_OK:
+        raise RuntimeError("16-bit form: device status " + fx.fxmig_strerror(fx.fxmig_check(b.ws_mig)))
+    ms = []
+    for _ in range(steps):
+        slab.copy_(slab0)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fx.fxmig_migrate_ex(d, lc, slab, b.vel, b.table, partials, 0, d.nz, b.ws_mig)
+        fx.fxmig_image(d, partials, image)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"ms_per_step": float(np.mean(ms)), "partials": nparts, "image": image.cpu().numpy()}
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -288,6 +379,14 @@ def run_native(args, w):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = world * w.points * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
 
+    learned, precs = None, {}
+    if world == 1 and not args.no_forms:
+        if d.L <= 15:
+            learned = measure_learned(fx, d, b, slab0, args.steps, flush, train_steps=args.train_steps)
+        for name in PREC_NAMES:
+            precs[name] = measure_precision(fx, d, b, slab0, args.steps, flush, launch,
+                                            getattr(fx, "FXMIG_PREC_" + name))
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -326,6 +425,7 @@ def run_native(args, w):
         "gpu_launches": (4 if args.mode != 2 else 2 + d.nz) * args.steps,
         "clocks": clk.summary(),
     }
+    img_ref = None
     if not args.no_cpu_baseline and world == 1:
         secs, P_ref, img_ref, cores = oracle_run(w, sec, vm)
         img_gpu = b.image.cpu().numpy()
@@ -336,6 +436,31 @@ def run_native(args, w):
                                 "t->f excluded)", "seconds": secs}
         line["parity"] = {"image_rel_l2": float(np.linalg.norm(img_gpu - img_ref) / np.linalg.norm(img_ref)),
                           "final_slice_rel_l2": float(np.linalg.norm(P_gpu - P_ref) / np.linalg.norm(P_ref))}
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))
+    img_plain = b.image.cpu().numpy()
+    forms = {}
+    for name, r in precs.items():
+        img_p = r.pop("image")
+        val_p = w.points / (r["ms_per_step"] * 1e-3)
+        forms[name.lower()] = {
+            "value": val_p, "unit": "point*freq/s", "speedup_vs_plain": val_p / value,
+            "what": "persistent form, wavefield lines and taps stored in 16 bits "
+                    + ("(taps as hi + lo)" if "SPLIT" in name else "") + ", FP32 arithmetic",
+            "image_rel_l2_vs_fp64_oracle": rel(img_p, img_ref) if img_ref is not None else None,
+            "image_rel_l2_vs_plain_gpu": rel(img_p, img_plain), **r}
+    if forms:
+        line["forms"] = forms
+    if learned is not None:
+        img_l = learned.pop("image")
+        val_l = w.points / (learned["ms_per_step"] * 1e-3)
+        line.setdefault("forms", {})
+        line["forms"]["learned"] = {
+            "value": val_l, "unit": "point*freq/s", "speedup_vs_plain": val_l / value,
+            "what": "operators generated by the network (split-BF16 tensor-core MLP) for every distinct "
+                    "(frequency, slowness) pair of each row; one Eq. 1 launch per depth row",
+            "image_rel_l2_vs_plain_gpu": rel(img_l, img_plain),
+            "image_rel_l2_vs_fp64_table_oracle": rel(img_l, img_ref) if img_ref is not None else None,
+            **learned}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -354,6 +479,8 @@ def main(argv=None):
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the learned-operator form")
+    ap.add_argument("--train-steps", type=int, default=100000, help="Adam steps of the operator network")
     ap.add_argument("--ref-freqs", type=int, default=24, help="frequencies per oracle step (reference arm)")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]

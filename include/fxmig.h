@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FXMIG_VERSION 1
+#define FXMIG_VERSION 2
 
 /* Return codes. */
 #define FXMIG_OK         0
@@ -60,6 +60,26 @@ extern "C" {
 #define FXMIG_MODE_AUTO       0
 #define FXMIG_MODE_PERSISTENT 1  /* one launch; each frequency line stays in shared memory for all depths */
 #define FXMIG_MODE_PER_DEPTH  2  /* one launch per depth step; the wavefield streams through L2/HBM */
+
+/* Storage precision of the persistent form (fxmig_launch.precision).  The
+ * arithmetic is FP32 in every form (packed f32x2 multiply-adds); what
+ * changes is how the wavefield lines kept in shared memory and the expanded
+ * operator taps are stored:
+ *   FP32        wavefield complex64, taps FP32
+ *   FP16, BF16  wavefield as two 16-bit floats per complex value (rounded to
+ *               nearest after every depth step), taps rounded to the same type
+ *   *_SPLIT     as FP16 / BF16, but each tap kept as a rounded 16-bit value plus
+ *               its rounded remainder (hi + lo), about 22 (FP16) or 16 (BF16)
+ *               significant bits
+ * 16-bit forms halve the shared memory per line, so more frequency lines fit
+ * a CTA (fewer waves of CTAs on large problems).  Compiled for the half
+ * lengths LT = 8, 12 and 17 (L <= 8, 9..12, 13..17); the public slab stays
+ * complex64. */
+#define FXMIG_PREC_FP32       0
+#define FXMIG_PREC_FP16       1
+#define FXMIG_PREC_BF16       2
+#define FXMIG_PREC_FP16_SPLIT 3
+#define FXMIG_PREC_BF16_SPLIT 4
 
 /* Problem description (all fields are read, none written).
  *   nx      traces, x_i = i dx, i in [0, nx)                        (Eq. 1's x_i)
@@ -84,9 +104,10 @@ typedef struct fxmig_desc {
  *                  form (1, 2, 4 or 8), 0 = choose
  *   groups         frequency groups (CTA clusters) in the persistent form, or
  *                  frequency tiles in the per-depth form; 0 = choose
- *   warps          warps per CTA (persistent form), 0 = choose */
+ *   warps          warps per CTA (persistent form), 0 = choose
+ *   precision      FXMIG_PREC_* (persistent form only; 0 = FP32) */
 typedef struct fxmig_launch {
-    int mode, cluster, groups, warps;
+    int mode, cluster, groups, warps, precision;
 } fxmig_launch;
 
 /* Library version (FXMIG_VERSION of the build). */

@@ -21,7 +21,8 @@ import os
 
 __all__ = [
     "FXMIG_OK", "FXMIG_EINVAL", "FXMIG_ENOSPC", "FXMIG_ECUDA", "FXMIG_ETIMEOUT", "FXMIG_EVELOCITY",
-    "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_WS_MLP_MIGRATE", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
+    "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_WS_MLP_MIGRATE", "FXMIG_PREC_FP32", "FXMIG_PREC_FP16",
+    "FXMIG_PREC_BF16", "FXMIG_PREC_FP16_SPLIT", "FXMIG_PREC_BF16_SPLIT", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
     "FxmigError", "Desc", "Launch", "lib", "library_path",
     "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
     "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
@@ -32,6 +33,7 @@ __all__ = [
 
 FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
 FXMIG_WS_T2F, FXMIG_WS_MIGRATE, FXMIG_WS_MLP_MIGRATE = 1, 2, 3
+FXMIG_PREC_FP32, FXMIG_PREC_FP16, FXMIG_PREC_BF16, FXMIG_PREC_FP16_SPLIT, FXMIG_PREC_BF16_SPLIT = 0, 1, 2, 3, 4
 FXMIG_MODE_AUTO, FXMIG_MODE_PERSISTENT, FXMIG_MODE_PER_DEPTH = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,7 +64,7 @@ class Desc(ctypes.Structure):
 class Launch(ctypes.Structure):
     """Mirror of ``fxmig_launch`` (zeros = automatic)."""
     _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
-                ("warps", ctypes.c_int)]
+                ("warps", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 def lib():

@@ -3,6 +3,11 @@
 // packed f32x2 FMAs, and the single-output FIR used for operator changes.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "fxmig_internal.cuh"
 
 namespace fxmig_impl {
@@ -79,24 +84,6 @@ __device__ __forceinline__ void fir8(const float2* __restrict__ wbase, const flo
     fir8_ptrs<LT>(wbase, tp, res, re);
 }
 
-// Store 8 outputs at padded positions LT + r relative to the 8-aligned base.
-template <int LT>
-__device__ __forceinline__ void store8(float2* base, const u64 (&res)[8]) {
-    if constexpr ((LT & 1) == 0) {
-#pragma unroll
-        for (int r = 0; r < 8; r += 2) {
-            const int t = LT + r;
-            *reinterpret_cast<ulonglong2*>(base + t + 2 * (t >> 3)) = make_ulonglong2(res[r], res[r + 1]);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int t = LT + r;
-            *reinterpret_cast<u64*>(base + t + 2 * (t >> 3)) = res[r];
-        }
-    }
-}
-
 __device__ __forceinline__ void load_s8(const float* p, float (&s8)[8]) {
     const float4 a = *reinterpret_cast<const float4*>(p);
     const float4 b = *reinterpret_cast<const float4*>(p + 4);
@@ -104,26 +91,146 @@ __device__ __forceinline__ void load_s8(const float* p, float (&s8)[8]) {
     s8[4] = b.x; s8[5] = b.y; s8[6] = b.z; s8[7] = b.w;
 }
 
-// Eq. 1 for 8 consecutive outputs that share one operator (taps of table row
-// idx0): the common case, one 16-byte tap load per tap for 8 outputs.
-template <int LT>
-__device__ __forceinline__ void fir8_shared_taps(const float2* __restrict__ wbase, int idx0,
-                                                 const float4* __restrict__ taps, u64 (&res)[8], float (&re)[8]) {
+// ------------------------------------------------- wavefield storage policies
+// How the persistent kernel keeps the wavefield in shared memory.  All
+// arithmetic is FP32 (packed f32x2 pairs (re, im)); the policies convert on
+// load and round on store.  ld2/st2 take an even padded position, which is
+// 16-byte aligned for 8-byte elements and 8-byte aligned for 4-byte ones.
+struct WsF32 {  // complex64
+    typedef float2 T;
+    static constexpr int kBytes = 8;
+    __device__ static __forceinline__ u64 ld1(const T* p) { return *reinterpret_cast<const u64*>(p); }
+    __device__ static __forceinline__ void ld2(const T* p, u64& a, u64& b) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void st1(T* p, u64 v) { *reinterpret_cast<u64*>(p) = v; }
+    __device__ static __forceinline__ void st2(T* p, u64 a, u64 b) {
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
+    }
+    __device__ static __forceinline__ T from_f2(float2 v) { return v; }
+    __device__ static __forceinline__ float2 to_f2(T v) { return v; }
+    __device__ static __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    __device__ static __forceinline__ void st_async(uint32_t addr, u64 v, uint32_t bar) {
+        st_async_v2(addr, f2_unpack(v), bar);
+    }
+};
+
+// complex value as two 16-bit floats (re in the low half), 4 bytes
+template <class H2>
+struct WsHalf {
+    typedef uint32_t T;
+    static constexpr int kBytes = 4;
+    __device__ static __forceinline__ float2 to_f2(T v) { return H2::to_f2(v); }
+    __device__ static __forceinline__ T from_f2(float2 v) { return H2::from_f2(v); }
+    __device__ static __forceinline__ u64 cvt(T v) {
+        const float2 f = to_f2(v);
+        return f2_pack(f.x, f.y);
+    }
+    __device__ static __forceinline__ T rnd(u64 v) { return from_f2(f2_unpack(v)); }
+    __device__ static __forceinline__ u64 ld1(const T* p) { return cvt(*p); }
+    __device__ static __forceinline__ void ld2(const T* p, u64& a, u64& b) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        a = cvt(v.x);
+        b = cvt(v.y);
+    }
+    __device__ static __forceinline__ void st1(T* p, u64 v) { *p = rnd(v); }
+    __device__ static __forceinline__ void st2(T* p, u64 a, u64 b) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(rnd(a), rnd(b));
+    }
+    __device__ static __forceinline__ T zero() { return 0u; }
+    __device__ static __forceinline__ void st_async(uint32_t addr, u64 v, uint32_t bar) {
+        asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+                     :: "r"(addr), "r"(rnd(v)), "r"(bar) : "memory");
+    }
+};
+struct H2F16 {
+    __device__ static __forceinline__ float2 to_f2(uint32_t v) {
+        __half2 h;
+        *reinterpret_cast<uint32_t*>(&h) = v;
+        return __half22float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float2 v) {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+};
+struct H2BF16 {
+    __device__ static __forceinline__ float2 to_f2(uint32_t v) {
+        __nv_bfloat162 h;
+        *reinterpret_cast<uint32_t*>(&h) = v;
+        return __bfloat1622float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float2 v) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+};
+typedef WsHalf<H2F16> WsF16;
+typedef WsHalf<H2BF16> WsBF16;
+
+// ------------------------------------------------------- tap storage policies
+// Kernel layout of one tap of the expanded operator table and its load as
+// the packed pairs (hr, hr) and (hi, hi).
+struct TapF32 {  // (hr, hr, hi, hi) in FP32, 16 bytes
+    typedef float4 E;
+    __device__ static __forceinline__ void ld(const E* p, u64& hr, u64& hi) { ldg_nc_v2(p, hr, hi); }
+};
+// 16-bit taps: (hr, hi) rounded to the half type (4 bytes), or with kSplit
+// the rounded pair and the rounded remainder, h = hi_part + lo_part (8 bytes).
+template <class H2, bool kSplit>
+struct TapHalf {
+    typedef typename std::conditional<kSplit, uint2, uint32_t>::type E;
+    __device__ static __forceinline__ void ld(const E* p, u64& hr, u64& hi) {
+        float2 h;
+        if constexpr (kSplit) {
+            const uint2 v = __ldg(p);
+            const float2 a = H2::to_f2(v.x), b = H2::to_f2(v.y);
+            h = make_float2(a.x + b.x, a.y + b.y);
+        } else {
+            h = H2::to_f2(__ldg(p));
+        }
+        hr = f2_pack(h.x, h.x);
+        hi = f2_pack(h.y, h.y);
+    }
+};
+
+// Store 8 outputs at padded positions LT + r relative to the 8-aligned base.
+template <int LT, class WS>
+__device__ __forceinline__ void store8(typename WS::T* base, const u64 (&res)[8]) {
+    if constexpr ((LT & 1) == 0) {
+#pragma unroll
+        for (int r = 0; r < 8; r += 2) {
+            const int t = LT + r;
+            WS::st2(base + t + 2 * (t >> 3), res[r], res[r + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int t = LT + r;
+            WS::st1(base + t + 2 * (t >> 3), res[r]);
+        }
+    }
+}
+
+// Eq. 1 for 8 consecutive outputs that share one operator (taps tp[0..LT]):
+// the common case, one tap load per tap for 8 outputs.  re: real parts of
+// the 8 input values at the output positions.
+template <int LT, class WS, class TP>
+__device__ __forceinline__ void fir8_shared_taps(const typename WS::T* __restrict__ wbase,
+                                                 const typename TP::E* __restrict__ tp, u64 (&res)[8],
+                                                 float (&re)[8]) {
     constexpr int NWIN = 8 + 2 * LT;
     u64 w[NWIN];
 #pragma unroll
-    for (int t = 0; t < NWIN; t += 2) {
-        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(wbase + t + 2 * (t >> 3));
-        w[t] = v.x;
-        w[t + 1] = v.y;
-    }
+    for (int t = 0; t < NWIN; t += 2) WS::ld2(wbase + t + 2 * (t >> 3), w[t], w[t + 1]);
 #pragma unroll
     for (int r = 0; r < 8; ++r) re[r] = f2_unpack(w[LT + r]).x;
-    const float4* tp = taps + (size_t)idx0 * (LT + 1);
     u64 A[8], B[8];
     {
         u64 hr, hi;
-        ldg_nc_v2(tp, hr, hi);
+        TP::ld(tp, hr, hi);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             A[r] = f2_mul(hr, w[LT + r]);
@@ -133,7 +240,7 @@ __device__ __forceinline__ void fir8_shared_taps(const float2* __restrict__ wbas
 #pragma unroll
     for (int n = 1; n <= LT; ++n) {
         u64 hr, hi;
-        ldg_nc_v2(tp + n, hr, hi);
+        TP::ld(tp + n, hr, hi);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const u64 t = f2_add(w[LT + r - n], w[LT + r + n]);
@@ -148,19 +255,18 @@ __device__ __forceinline__ void fir8_shared_taps(const float2* __restrict__ wbas
     }
 }
 
-// Eq. 1 for one output at local position x with its own operator idx.
-template <int LT>
-__device__ __forceinline__ u64 fir1(const float2* __restrict__ line, int x, int idx, const float4* __restrict__ taps) {
-    const float4* tp = taps + (size_t)idx * (LT + 1);
+// Eq. 1 for one output at local position x of a line, with taps tp[0..LT].
+template <int LT, class WS, class TP>
+__device__ __forceinline__ u64 fir1(const typename WS::T* __restrict__ line, int x,
+                                    const typename TP::E* __restrict__ tp) {
     u64 hr, hi;
-    ldg_nc_v2(tp, hr, hi);
-    const u64 c = *reinterpret_cast<const u64*>(line + phys(x + LT));
+    TP::ld(tp, hr, hi);
+    const u64 c = WS::ld1(line + phys(x + LT));
     u64 A = f2_mul(hr, c), B = f2_mul(hi, c);
 #pragma unroll
     for (int n = 1; n <= LT; ++n) {
-        ldg_nc_v2(tp + n, hr, hi);
-        const u64 t = f2_add(*reinterpret_cast<const u64*>(line + phys(x + LT - n)),
-                             *reinterpret_cast<const u64*>(line + phys(x + LT + n)));
+        TP::ld(tp + n, hr, hi);
+        const u64 t = f2_add(WS::ld1(line + phys(x + LT - n)), WS::ld1(line + phys(x + LT + n)));
         A = f2_fma(hr, t, A);
         B = f2_fma(hi, t, B);
     }

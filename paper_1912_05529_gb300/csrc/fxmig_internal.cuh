@@ -164,6 +164,7 @@ __device__ __forceinline__ void st_cluster_v2(uint32_t addr, float2 v) {
 // ------------------------------------------------------------ host interfaces
 struct MigratePlan {
     int mode;      // FXMIG_MODE_PERSISTENT or FXMIG_MODE_PER_DEPTH
+    int precision; // FXMIG_PREC_*
     int LT;        // compiled half-length >= L
     int cluster;   // persistent: CTAs per frequency group along x
     int groups;    // persistent: frequency groups; per-depth: frequency tiles
@@ -173,6 +174,7 @@ struct MigratePlan {
     int W;         // persistent: x segment per CTA (multiple of 8)
     int lines;     // persistent: max lines per group
     size_t smem;   // dynamic shared memory bytes per CTA
+    int img;       // persistent: imaging buffer in shared memory
     int nparts;    // partial images written
 };
 
@@ -192,6 +194,11 @@ cudaError_t launch_t2f(const fxmig_desc* d, const float* section, void* slab, vo
 cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* vel,
                            const void* table, float* partials, int z_begin, int z_end, void* ws,
                            cudaStream_t s, bool precompute_slowness);
+// 16-bit storage forms of the persistent kernel (migrate_rp.cu)
+struct MigrateArgs;
+bool rp_compiled(int LT);
+cudaError_t expand_taps_rp(int precision, const float2* table, int nk, int L, int LT, void* taps, cudaStream_t s);
+cudaError_t launch_persistent_rp(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s);
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
                          cudaStream_t s);
 

@@ -1,0 +1,437 @@
+// persistent.cuh -- the persistent form of the depth loop (Algorithm 1; Eq. 1;
+// Sec. III per-point operator lookup), templated on the half-length LT and on
+// how the wavefield (WsF32 / WsF16 / WsBF16) and the operator taps
+// (TapF32 / TapHalf) are stored.  Arithmetic is FP32 in every form.
+//
+// A cluster of C CTAs owns a group of frequency lines; CTA r of the cluster
+// keeps x-segment r of every line of the group in shared memory for ALL depth
+// steps.  Per depth step each CTA
+//   - sums Re P over its lines into its partial image row (deterministic),
+//   - looks up the operator of every output point (fp32 index, Sec. III),
+//   - applies Eq. 1 with symmetric-pair packed f32x2 FMAs,
+//   - pushes the L edge outputs into its neighbours' halos (st.async, DSMEM),
+// and one CTA barrier replaces the paper's kernel exit (Sec. III, V).  The
+// slowness (or velocity) row of a later depth is staged by a 1-D TMA bulk
+// copy while the current depth is computed.
+#pragma once
+
+#include <float.h>
+
+#include "fir.cuh"
+#include "fxmig_internal.cuh"
+
+namespace fxmig_impl {
+
+struct MigrateArgs {
+    int nx, nz, nw, nk, z_begin, z_end, i0, nt;
+    double dt, dk;
+    float2* slab;           // [nw][nx]
+    const float* vel;       // [nz][nx]
+    const float* slow;      // [nz][nx] fl32(1/vel) precomputed, or nullptr (converted in the kernel)
+    const void* taps;       // [nk][LT+1] taps in the kernel's tap layout (TapF32 / TapHalf)
+    float* partials;        // [G][nz][nx]
+    int* status;
+    int W, C, G, lines, tma_ok;
+    int cwarps, ewarps;     // persistent: interior compute warps, edge warps
+    int img;                // persistent: imaging buffer in shared memory (persistent_layout)
+    // per-depth form
+    const float2* in;
+    float2* out;
+    int z;
+};
+
+struct PersistentSmem {
+    size_t mbar, qs, vbuf, sbuf, img, wave, total;
+};
+constexpr int kRowSlots = 7;  // ring of staged slowness/velocity rows
+constexpr int kRowAhead = kRowSlots - 1;  // rows are staged this many depth steps ahead
+// esize: bytes of one stored wavefield value (8 FP32 complex, 4 half complex).
+// img: keep Re P of every line in an imaging buffer [2][lines][W] (reduced
+// after the step barrier, off the critical path) instead of summing the
+// image row from the wavefield before the barrier; costs 8 W bytes per line.
+__host__ __device__ inline PersistentSmem persistent_layout(int W, int lines, int LT, int esize, bool img) {
+    PersistentSmem s;
+    s.mbar = 0;
+    s.qs = 8 * (kRowSlots + 4);  // row-staging barriers, then halo barriers [side][parity]
+    s.vbuf = align16(s.qs + 4 * (size_t)lines);
+    s.sbuf = s.vbuf + kRowSlots * (size_t)W * 4;
+    s.img = align16(s.sbuf + 2 * (size_t)W * 4);
+    s.wave = align16(s.img + (img ? 2 * (size_t)lines * W * 4 : 0));
+    s.total = s.wave + 2 * (size_t)lines * seg_phys_len(W, LT) * esize;
+    return s;
+}
+
+// ------------------------------------------------------------ persistent form
+constexpr int kPersistentMaxThreads = 384;  // up to 12 warps: 168 registers per thread
+
+// Per-CTA constants of the persistent kernel.
+struct SegCtx {
+    int W, SP, wv, rank, C, nk;
+    bool has_left, has_right;    // cluster neighbours exist on that side
+    uint32_t nb_left, nb_right;  // neighbours' wave base (shared::cluster address)
+    // halo barriers of the neighbours that receive this CTA's edge outputs:
+    // the left neighbour's right-halo barrier and the right neighbour's
+    // left-halo barrier, for the parity of the receiving depth step
+    uint32_t bar_left[2], bar_right[2];
+};
+
+// Send output x of line s (value v) to the neighbours whose halo holds it.
+template <int LT, class WS>
+__device__ __forceinline__ void push_halo(const SegCtx& g, size_t nxt_off, int s, int x, u64 v, int pb) {
+    if (g.has_left && x < LT)
+        WS::st_async(g.nb_left + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(g.W + LT + x)) * WS::kBytes), v,
+                     g.bar_left[pb]);
+    if (g.has_right && x >= g.W - LT)
+        WS::st_async(g.nb_right + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(x - g.W + LT)) * WS::kBytes), v,
+                     g.bar_right[pb]);
+}
+
+// Write one output (local position x of line s) to the next buffer and, when
+// `push` is set and it lies within LT of a segment edge, into the halo of the
+// neighbour on that side (st.async, counted on the neighbour's halo barrier
+// of parity pb).
+template <int LT, class WS>
+__device__ __forceinline__ void put_output(const SegCtx& g, typename WS::T* nxt, size_t nxt_off, int s, int x,
+                                           u64 v, bool push, int pb) {
+    WS::st1(nxt + (size_t)s * g.SP + phys(x + LT), v);
+    if (push) push_halo<LT, WS>(g, nxt_off, s, x, v, pb);
+}
+
+// One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
+// extrapolated with the operator of the first output.  Returns the mask of
+// outputs whose own operator differs (the velocity changes inside the 8):
+// those are left unwritten for fir1.  With an imaging buffer (imgz), the real
+// parts of the current wavefield go there.
+template <int LT, class WS, class TP>
+__device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, bool edge, bool push, int pb,
+                                              const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
+                                              const float* srow, const float* qs, float* imgz,
+                                              const typename TP::E* __restrict__ taps) {
+    float s8[8];
+    load_s8(srow + xl0, s8);
+    const float q = qs[s];
+    const int idx0 = table_index(q, s8[0], g.nk);
+    uint32_t skip = 0;
+    bool same = true;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
+    if (!same) {
+        const int nvalid = min(8, g.wv - xl0);
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+            if (r < nvalid && table_index(q, s8[r], g.nk) != idx0) skip |= 1u << r;
+    }
+    u64 res[8];
+    float re[8];
+    fir8_shared_taps<LT, WS, TP>(cur + (size_t)s * g.SP + (xl0 >> 3) * 10, taps + (size_t)idx0 * (LT + 1), res,
+                                 re);
+    if (imgz) {  // real parts of the step's input, for the imaging buffer
+        *reinterpret_cast<float4*>(imgz + (size_t)s * g.W + xl0) = make_float4(re[0], re[1], re[2], re[3]);
+        *reinterpret_cast<float4*>(imgz + (size_t)s * g.W + xl0 + 4) = make_float4(re[4], re[5], re[6], re[7]);
+    }
+    if (xl0 + 8 > g.wv) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (xl0 + r >= g.wv) res[r] = 0ull;
+    }
+    if (skip == 0) {
+        store8<LT, WS>(nxt + (size_t)s * g.SP + (xl0 >> 3) * 10, res);
+        if (edge && push) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) push_halo<LT, WS>(g, nxt_off, s, xl0 + r, res[r], pb);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (!((skip >> r) & 1u)) put_output<LT, WS>(g, nxt, nxt_off, s, xl0 + r, res[r], edge && push, pb);
+    }
+    return skip;
+}
+
+// Warp-cooperative recomputation of the outputs flagged in each lane's
+// `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
+// numbered and taken one per lane.  All 32 lanes must call.
+template <int LT, class WS, class TP>
+__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0,
+                                            const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
+                                            const float* srow, const float* qs,
+                                            const typename TP::E* __restrict__ taps, int lane, bool push, int pb) {
+    const uint32_t cnt = __popc(mask);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    const uint32_t excl = incl - cnt;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t it = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            const uint32_t ex = __shfl_sync(0xffffffffu, excl, cand);
+            if (ex <= it) owner = cand;
+        }
+        const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
+        const int s_o = __shfl_sync(0xffffffffu, s, owner);
+        const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
+        if (it < total) {
+            const int r = (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
+            const int x = x0_o + r;
+            const int idx = table_index(qs[s_o], srow[x], g.nk);
+            put_output<LT, WS>(g, nxt, nxt_off, s_o, x,
+                               fir1<LT, WS, TP>(cur + (size_t)s_o * g.SP, x, taps + (size_t)idx * (LT + 1)), push,
+                               pb);
+        }
+    }
+}
+
+template <int LT, class WS, class TP>
+__global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
+    typedef typename WS::T T;
+    const typename TP::E* __restrict__ taps = static_cast<const typename TP::E*>(a.taps);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int W = a.W, m = a.lines, C = a.C;
+    const int SP = seg_phys_len(W, LT);
+    const int NC = W >> 3;
+    const PersistentSmem L = persistent_layout(W, m, LT, WS::kBytes, a.img != 0);
+    float* img = a.img ? reinterpret_cast<float*>(smem + L.img) : nullptr;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
+    float* qs = reinterpret_cast<float*>(smem + L.qs);
+    float* vbuf = reinterpret_cast<float*>(smem + L.vbuf);
+    float* sbuf = reinterpret_cast<float*>(smem + L.sbuf);
+    T* wave = reinterpret_cast<T*>(smem + L.wave);
+
+    const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+    const int g = blockIdx.x / C;
+    const int l_begin = (int)(((long long)g * a.nw) / a.G);
+    const int mg = (int)(((long long)(g + 1) * a.nw) / a.G) - l_begin;
+    const int x0 = rank * W;
+    const int wv = max(0, min(W, a.nx - x0));
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nthr >> 5;
+
+    // ---- prologue: zero both wavefield buffers (halos outside [0, nx) stay 0)
+    for (int i = tid; i < 2 * m * SP; i += nthr) wave[i] = WS::zero();
+    for (int s = tid; s < m; s += nthr) qs[s] = (s < mg) ? q_of_line(a.i0, l_begin + s, a.nt, a.dt, a.dk) : 0.f;
+    uint64_t* hbar = mbar + kRowSlots;  // [side 0 left, 1 right][parity]
+    if (tid == 0) {
+        for (int b = 0; b < kRowSlots + 4; ++b) mbar_init(&mbar[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // wavefield at depth z_begin, with halos read from the neighbours' x range
+    for (int s = 0; s < mg; ++s) {
+        const float2* src = a.slab + (size_t)(l_begin + s) * a.nx;
+        T* dst = wave + (size_t)s * SP;
+        for (int pos = tid; pos < W + 2 * LT; pos += nthr) {
+            const int x = x0 - LT + pos;
+            if (x >= 0 && x < a.nx) dst[phys(pos)] = WS::from_f2(src[x]);
+        }
+    }
+
+    // Row staging.  Row z of the slowness field (precomputed, a.slow) or of
+    // the velocity (converted here) goes through slot z % kRowSlots of vbuf by
+    // a 1-D bulk copy, issued kRowAhead depth steps ahead.  The k-th use of a
+    // slot completes mbarrier phase k, so row z waits on parity
+    // ((z - z_begin) / kRowSlots) & 1; every thread that reads the row waits.
+    const float* rows = a.slow ? a.slow : a.vel;
+    auto issue_row = [&](int z) {  // one thread
+        if (!a.tma_ok) return;
+        const int b = z % kRowSlots;
+        const uint32_t bytes = (uint32_t)wv * 4u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&mbar[b], bytes);
+        if (bytes) bulk_g2s(vbuf + b * W, rows + (size_t)z * a.nx + x0, bytes, &mbar[b]);
+    };
+    auto wait_row = [&](int z) {
+        if (!a.tma_ok) return;
+        const int b = z % kRowSlots;
+        if (!mbar_wait_bounded(&mbar[b], (uint32_t)(((z - a.z_begin) / kRowSlots) & 1), kWaitPolls))
+            atomicOr(a.status, kStatusTimeout);
+    };
+    auto srow_of = [&](int z) -> const float* {
+        if (a.slow) return a.tma_ok ? (vbuf + (z % kRowSlots) * W) : (a.slow + (size_t)z * a.nx + x0);
+        return sbuf + (z & 1) * W;
+    };
+    // s = fl32(1/v) for the CTA's x segment (only without precomputed slowness)
+    auto convert_row = [&](int z) {
+        if (a.slow) return;
+        const float* src = a.tma_ok ? (vbuf + (z % kRowSlots) * W) : (a.vel + (size_t)z * a.nx + x0);
+        float* dst = sbuf + (z & 1) * W;
+        bool bad = false;
+        for (int x = tid; x < W; x += nthr) {
+            float s = 0.f;
+            if (x < wv) {
+                const float v = src[x];
+                bad |= !(v > 0.f && v <= FLT_MAX);
+                s = __frcp_rn(v);
+            }
+            dst[x] = s;
+        }
+        if (bad) atomicOr(a.status, kStatusVelocity);
+    };
+    // partial[g][z][x0 + x] = sum over the group's lines (ascending) of Re P at
+    // depth z: from the imaging buffer after the step barrier, or (no buffer)
+    // from the step's input wavefield, which nobody writes during the step,
+    // before the barrier
+    auto reduce_image_row = [&](int z, const T* cur) {
+        float* dst = a.partials + ((size_t)g * a.nz + z) * a.nx + x0;
+        if (img) {
+            const float* src = img + (size_t)(z & 1) * m * W;
+            for (int x = tid * 4; x < wv; x += nthr * 4) {
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int s = 0; s < mg; ++s) {
+                    const float4 v = *reinterpret_cast<const float4*>(src + (size_t)s * W + x);
+                    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+                }
+                if (x + 4 <= wv && (a.nx & 3) == 0) {
+                    *reinterpret_cast<float4*>(dst + x) = acc;
+                } else {
+                    const float t[4] = {acc.x, acc.y, acc.z, acc.w};
+                    for (int i = 0; i < 4 && x + i < wv; ++i) dst[x + i] = t[i];
+                }
+            }
+        } else {
+            for (int x = tid; x < wv; x += nthr) {
+                float acc = 0.f;
+                for (int s = 0; s < mg; ++s) acc += WS::to_f2(cur[(size_t)s * SP + phys(x + LT)]).x;
+                dst[x] = acc;
+            }
+        }
+    };
+
+    if (tid == 0)
+        for (int zz = a.z_begin; zz < min(a.z_end, a.z_begin + kRowAhead); ++zz) issue_row(zz);
+    wait_row(a.z_begin);
+    convert_row(a.z_begin);
+    // every CTA of the cluster has zeroed its buffers before any halo push
+    if (C > 1) cluster_sync_all(); else __syncthreads();
+
+    SegCtx sc;
+    sc.W = W; sc.SP = SP; sc.wv = wv; sc.rank = rank; sc.C = C; sc.nk = a.nk;
+    sc.has_left = C > 1 && rank > 0;
+    sc.has_right = C > 1 && rank < C - 1;
+    sc.nb_left = sc.has_left ? map_cluster_rank(wave, rank - 1) : 0u;
+    sc.nb_right = sc.has_right ? map_cluster_rank(wave, rank + 1) : 0u;
+    for (int b = 0; b < 2; ++b) {
+        sc.bar_left[b] = sc.has_left ? map_cluster_rank(&hbar[2 + b], rank - 1) : 0u;   // its right halo
+        sc.bar_right[b] = sc.has_right ? map_cluster_rank(&hbar[b], rank + 1) : 0u;     // its left halo
+    }
+    // bytes each halo barrier phase receives: LT outputs of every line
+    const uint32_t halo_bytes = (uint32_t)mg * LT * (uint32_t)WS::kBytes;
+
+    // Work items: (line, 8-output chunk), one per lane and round.  Chunks
+    // within LT of a segment edge ("edge" chunks) read the halo and send their
+    // outputs to the neighbours' halos.  Halo exchange is point to point:
+    // outputs go out with st.async, and a CTA waits on its own halo barrier
+    // of the step's parity before it reads its halo; neighbours can never be
+    // more than one step apart, so two parities suffice and no cluster-wide
+    // barrier is needed.  One CTA barrier ends a depth step; the image row of
+    // the step is summed right after it from the imaging buffer (overlapping
+    // the next step's items), or without that buffer just before it from the
+    // step's input wavefield.
+    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
+    const int n_items = mg * NC;
+
+    for (int z = a.z_begin; z < a.z_end; ++z) {
+        const int zb = (z - a.z_begin) & 1;
+        const T* cur = wave + (size_t)zb * m * SP;
+        T* nxt = wave + (size_t)(zb ^ 1) * m * SP;
+        float* imgz = img ? img + (size_t)(z & 1) * m * W : nullptr;
+        const size_t nxt_off = (size_t)(zb ^ 1) * m * SP;
+        const float* srow = srow_of(z);
+        const bool push = (C > 1) && (z + 1 < a.z_end);  // outputs feed a further step
+        const int pb = (z + 1) & 1;                         // receivers' barrier parity
+        const bool halo_wait = (C > 1) && (z > a.z_begin);
+        const uint32_t hpar = (uint32_t)(((z - a.z_begin - 1) >> 1) & 1);
+        if (tid == 0) {
+            // row z+kRowAhead goes to the slot of row z-1, which nobody reads now
+            if (z + kRowAhead < a.z_end) issue_row(z + kRowAhead);
+            if (halo_wait) {
+                if (sc.has_left) mbar_arrive_expect_tx(&hbar[z & 1], halo_bytes);
+                if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes);
+            }
+        }
+        if (a.slow && z > a.z_begin) wait_row(z);  // (converted rows were synchronised)
+
+        for (int base = warp * 32; base < n_items; base += nwarps * 32) {
+            const int item = base + lane;
+            int s = 0, xl0 = 0;
+            bool work = false, edge = false;
+            if (item < n_items) {
+                s = item / NC;
+                const int c = item - s * NC;
+                xl0 = c << 3;
+                work = xl0 < wv;
+                edge = (C > 1) && (c < E || c >= NC - E);
+            }
+            if (halo_wait && __any_sync(0xffffffffu, edge)) {
+                // the neighbours' outputs of step z-1 have landed in cur's halo
+                bool ok = true;
+                if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+            }
+            uint32_t mask = 0;
+            if (work) {
+                mask = main_item<LT, WS, TP>(sc, s, xl0, edge, push, pb, cur, nxt, nxt_off, srow, qs, imgz, taps);
+            } else if (edge && push && item < n_items) {
+                // beyond the line end: the neighbours still expect zeros
+#pragma unroll
+                for (int r = 0; r < 8; ++r) push_halo<LT, WS>(sc, nxt_off, s, xl0 + r, 0ull, pb);
+            }
+            if (__any_sync(0xffffffffu, mask != 0u))
+                coop_fixups<LT, WS, TP>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, taps, lane, push, pb);
+        }
+        if (!a.slow && z + 1 < a.z_end) {
+            // velocity rows are converted by the whole CTA before the next step
+            wait_row(z + 1);
+            convert_row(z + 1);
+        }
+        if (!img) reduce_image_row(z, cur);
+        __syncthreads();
+        if (img) reduce_image_row(z, cur);  // img[z & 1] is next written at step z + 2
+    }
+    // nothing is pushed at the last step and every earlier push has been
+    // waited for; the final barrier keeps the CTAs' exits ordered
+    if (C > 1) cluster_sync_all(); else __syncthreads();
+
+    const T* fin = wave + (size_t)((a.z_end - a.z_begin) & 1) * m * SP;
+    for (int s = 0; s < mg; ++s) {
+        float2* dst = a.slab + (size_t)(l_begin + s) * a.nx + x0;
+        for (int x = tid; x < wv; x += nthr) dst[x] = WS::to_f2(fin[(size_t)s * SP + phys(x + LT)]);
+    }
+}
+
+
+// One launch of the persistent form for compiled LT and storage policies.
+template <int LT, class WS, class TP>
+cudaError_t launch_persistent(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
+    auto kern = k_migrate_persistent<LT, WS, TP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e != cudaSuccess) return e;
+    if (plan.cluster > 1) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.groups * plan.cluster);
+    cfg.blockDim = dim3(plan.warps * 32);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = plan.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace fxmig_impl

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(fx):
 
 
 def test_version_and_strerror(fx):
-    assert fx.fxmig_version() == 1
+    assert fx.fxmig_version() == 2
     for code in (0, -1, -2, -3, -4, -5):
         assert fx.fxmig_strerror(code) and fx.fxmig_strerror(code) != "unknown error"
     assert fx.fxmig_strerror(-99) == "unknown error"
@@ -117,3 +117,53 @@ def test_invalid_launch_choices(fx):
     d = _desc(fx)
     assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(mode=7))) == fx.FXMIG_EINVAL
     assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(cluster=3))) == fx.FXMIG_EINVAL
+
+
+def test_precision_choices(fx):
+    lib = fx.lib()
+    d = _desc(fx)
+    npart = lambda **kw: lib.fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(**kw)))
+    assert npart(precision=fx.FXMIG_PREC_FP16) > 0
+    assert npart(precision=fx.FXMIG_PREC_BF16_SPLIT) > 0
+    assert npart(precision=5) == fx.FXMIG_EINVAL
+    assert npart(precision=-1) == fx.FXMIG_EINVAL
+    # the per-depth form has no 16-bit storage form
+    assert npart(mode=fx.FXMIG_MODE_PER_DEPTH, precision=fx.FXMIG_PREC_FP16) == fx.FXMIG_EINVAL
+    # 16-bit forms are compiled for LT = 8, 12, 17 only
+    d20 = _desc(fx, L=20)
+    assert lib.fxmig_num_partials(ctypes.byref(d20), ctypes.byref(fx.Launch(precision=1))) == fx.FXMIG_EINVAL
+    assert lib.fxmig_num_partials(ctypes.byref(d20), None) > 0
+
+
+def test_large_problem_plans_several_waves(fx):
+    # 8192 traces x 601 frequencies do not fit one wave of CTAs in shared
+    # memory: the plan takes more frequency groups; 16-bit storage needs fewer
+    d = fx.desc_for(nx=8192, nz=2000, nt=4000, dx=6.25, dz=4.0, dt=0.002, f_lo=5.0, f_hi=80.0, L=17,
+                    v_min=750.0)
+    assert d.nw == 601
+    n32 = fx.fxmig_num_partials(d, fx.Launch(cluster=8))
+    n16 = fx.fxmig_num_partials(d, fx.Launch(cluster=8, precision=fx.FXMIG_PREC_FP16))
+    assert n32 * 8 > 152 and n16 < n32
+
+
+def test_learned_operator_entry_points_reject_bad_arguments(fx):
+    lib = fx.lib()
+    d = _desc(fx)
+    ok = ctypes.c_void_p(1 << 20)
+    assert fx.fxmig_mlp_param_count(12) == 10138
+    assert lib.fxmig_mlp_param_count(16) == fx.FXMIG_EINVAL
+    assert lib.fxmig_mlp_train_ws_bytes(12, 0) == 0
+    assert lib.fxmig_mlp_num_partials(ctypes.byref(_desc(fx, L=17))) == fx.FXMIG_EINVAL
+    assert lib.fxmig_mlp_num_partials(ctypes.byref(d)) > 0
+    assert lib.fxmig_design_at(ctypes.byref(d), ok, -1, ok, None, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_design_at(ctypes.byref(d), None, 4, ok, None, None) == fx.FXMIG_EINVAL
+    ws = fx.fxmig_mlp_train_ws_bytes(12, 100)
+    assert lib.fxmig_mlp_train(ctypes.byref(d), None, ok, ok, 0, 1, 1e-3, 1e-3, 0, ok, ok, 100, None, ok, ws,
+                               None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_mlp_train(ctypes.byref(d), ok, ok, ok, 0, 1, 1e-3, 1e-3, 0, ok, ok, 100, None, ok, ws - 1,
+                               None) == fx.FXMIG_ENOSPC
+    assert lib.fxmig_mlp_grad(ctypes.byref(d), ok, ok, ok, 0, ok, None, ok, ws, None) == fx.FXMIG_EINVAL
+    need = fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MLP_MIGRATE)
+    assert need > 0
+    assert lib.fxmig_mlp_migrate(ctypes.byref(d), ok, ok, None, ok, 64, 0, 5, ok, need, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_mlp_migrate(ctypes.byref(d), ok, ok, ok, ok, 64, 0, 5, ok, need - 1, None) == fx.FXMIG_ENOSPC
