@@ -295,6 +295,225 @@ def measure_precision(fx, d, b, slab0, steps, flush, launch, prec):
     return {"ms_per_step": float(np.mean(ms)), "partials": nparts, "image": image.cpu().numpy()}
 
 
+# ------------------------------------------------------------ batched lines
+BATCH_NAME = "batched_64"
+
+
+def batch_inputs(seed0: int):
+    """64 uneven lines (seeded Nx, Nz, band, L), each with its own seeded
+    layered velocity model; the wavefield at the surface is a seeded random
+    band of complex values (the migration's cost does not depend on them)."""
+    out = []
+    for w in W.batched_lines(64, seed0=seed0):
+        v, _ = W.layered_lens_model(w, lens=False)
+        vm = (0.5 * v).astype(np.float32)
+        rng = np.random.default_rng(w.seed + 77)
+        P0 = (rng.standard_normal((w.nw, w.nx)) + 1j * rng.standard_normal((w.nw, w.nx))).astype(np.complex64)
+        out.append((w, vm, P0))
+    return out
+
+
+def run_batch(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1912_05529_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1912_05529_gb300 as fx
+
+    inputs = batch_inputs(1000 + 1000 * rank)
+    bufs = []
+    for w, vm, P0 in inputs:
+        d = fx.Desc(nx=w.nx, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz, dt=w.dt,
+                    theta_max_deg=w.theta_deg, k_max=k_max_of(w, float(vm.min())))
+        b = dict(d=d, w=w, slab0=torch.from_numpy(P0).cuda(), vel=torch.from_numpy(vm).cuda(),
+                 table=torch.empty((w.nk, w.L + 1), dtype=torch.complex64, device="cuda"),
+                 image=torch.empty((w.nz, w.nx), dtype=torch.float32, device="cuda"))
+        b["slab"] = b["slab0"].clone()
+        fx.fxmig_design_operators(d, b["table"])
+        bufs.append(b)
+    points = sum(b["w"].points for b in bufs)
+    ops = sum(b["w"].points * ops_per_point(b["w"].L) for b in bufs)
+
+    def lines_for(plan):
+        nparts = fx.fxmig_batch_num_partials([fx.Line(d=b["d"]) for b in bufs], plan)
+        out = []
+        for b, p in zip(bufs, nparts):
+            b["partials"] = torch.empty((p, b["d"].nz, b["d"].nx), dtype=torch.float32, device="cuda")
+            out.append(fx.line_of(b["d"], b["slab"], b["vel"], b["table"], b["partials"]))
+        return out
+
+    # autotune on scratch copies, then the chosen plan
+    lines = lines_for(None)
+    ws_t = torch.empty(fx.fxmig_batch_workspace_bytes(lines, autotune=True), dtype=torch.uint8, device="cuda")
+    plan, tune_ms = fx.fxmig_batch_autotune(lines, ws_t)
+    del ws_t
+    lines = lines_for(plan)
+    ws = torch.empty(fx.fxmig_batch_workspace_bytes(lines), dtype=torch.uint8, device="cuda")
+
+    def step():
+        fx.fxmig_migrate_batch(lines, plan, ws)
+        for b in bufs:
+            fx.fxmig_image(b["d"], b["partials"], b["image"])
+
+    def restore():
+        for b in bufs:
+            b["slab"].copy_(b["slab0"])
+
+    restore()
+    step()   # eager run (kernel attributes), then capture the whole step in one graph
+    torch.cuda.synchronize()
+    if fx.fxmig_check(ws) != fx.FXMIG_OK:
+        raise RuntimeError("batch: device status " + fx.fxmig_strerror(fx.fxmig_check(ws)))
+    graph = torch.cuda.CUDAGraph()
+    restore()
+    with torch.cuda.graph(graph):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        restore()
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = []
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        for _ in range(args.steps):
+            restore()
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    tot_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * points * args.steps / (tot_ms * 1e-3)
+    img_gpu = [b["image"].cpu().numpy() for b in bufs]
+
+    # end to end: wavefields and velocities from pinned host memory, the
+    # captured step, images back to pinned host memory
+    slab_h = [torch.from_numpy(P0).pin_memory() for _, _, P0 in inputs]
+    vel_h = [torch.from_numpy(vm).pin_memory() for _, vm, _ in inputs]
+    img_h = [torch.empty((b["d"].nz, b["d"].nx), dtype=torch.float32, pin_memory=True) for b in bufs]
+    e2e_ms = []
+    for it in range(args.steps + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b, sh, vh in zip(bufs, slab_h, vel_h):
+            b["slab"].copy_(sh, non_blocking=True)
+            b["vel"].copy_(vh, non_blocking=True)
+        graph.replay()
+        for b, ih in zip(bufs, img_h):
+            ih.copy_(b["image"], non_blocking=True)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_val = world * points * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
+    h2d = sum(P0.nbytes + vm.nbytes for _, vm, P0 in inputs)
+    d2h = sum(b["d"].nz * b["d"].nx * 4 for b in bufs)
+
+    # the comparison forms, once each: a persistent launch per line, and one
+    # launch per line per depth step
+    def per_line(launch):
+        total = 0.0
+        for b in bufs:
+            d = b["d"]
+            n = fx.fxmig_num_partials(d, launch)
+            parts = torch.empty((n, d.nz, d.nx), dtype=torch.float32, device="cuda")
+            wsl = torch.empty(fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MIGRATE), dtype=torch.uint8, device="cuda")
+            b["slab"].copy_(b["slab0"])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fx.fxmig_migrate_ex(d, launch, b["slab"], b["vel"], b["table"], parts, 0, d.nz, wsl)
+            fx.fxmig_image(d, parts, b["image"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+    per_line(None)   # warm-up (kernel attributes, first-touch)
+    t_persistent = per_line(None)
+    t_per_depth = per_line(fx.Launch(mode=fx.FXMIG_MODE_PER_DEPTH))
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peaks, peak_src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", NOMINAL_SM_MHZ))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tops = sms * 128 * sm_max * 1e6 / 1e12
+    mean_ms = tot_ms / args.steps
+    achieved = ops / (mean_ms * 1e-3) / 1e12
+    line = {
+        "metric": "extrapolated points*freq/s (Nx*Nz*Nw/s)", "value": value, "unit": "point*freq/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (64 seeded layered models, seeded random surface wavefields)",
+        "config": {"workload": BATCH_NAME, "lines": len(bufs), "points": points,
+                   "nx": [min(b["d"].nx for b in bufs), max(b["d"].nx for b in bufs)],
+                   "nz": [min(b["d"].nz for b in bufs), max(b["d"].nz for b in bufs)],
+                   "nw": [min(b["d"].nw for b in bufs), max(b["d"].nw for b in bufs)],
+                   "L": sorted({b["d"].L for b in bufs}),
+                   "plan": {"cluster": plan.cluster, "lines_cap": plan.lines_cap, "autotune_ms": tune_ms},
+                   "launch": "one persistent batch kernel + per-line imaging, replayed as one CUDA graph",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"{world} independent batches" if world > 1 else "1 batch"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s (FP32 pipe)",
+                     "frac": achieved / peak_tops, "traffic": None, "kernel": "k_migrate_batch",
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
+                     "ops_per_point": "6L+4 per line"},
+        "e2e": {"value": e2e_val, "unit": "point*freq/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "includes": "H2D wavefields+velocities, batch depth loop, imaging, D2H images"},
+        "gpu_launches": (2 + len(bufs)) * args.steps,
+        "clocks": clk.summary(),
+        "compare": {
+            "per_line_persistent": {"ms": t_persistent, "value": points / (t_persistent * 1e-3),
+                                    "batch_speedup": t_persistent / mean_ms},
+            "per_line_per_depth": {"ms": t_per_depth, "value": points / (t_per_depth * 1e-3),
+                                   "batch_speedup": t_per_depth / mean_ms,
+                                   "launches": sum(b["d"].nz for b in bufs)}},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        small = sorted(range(len(inputs)), key=lambda i: inputs[i][0].points)[:2]
+        secs, errs, pts = 0.0, [], 0
+        import oracle as O
+        O.build()
+        for i in small:
+            w, vm, P0 = inputs[i]
+            om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+            k_max = float(om[-1] / float(vm.min()))
+            table = O.design_operators(w.nk, k_max, w.dx, w.dz, w.L, w.theta_deg).astype(np.complex64)
+            _, dk = O.k_grid(w.nk, k_max)
+            ts = time.perf_counter()
+            _, img_ref = O.migrate(P0.astype(np.complex128), vm, table.astype(np.complex128), O.q_values(om, dk))
+            secs += time.perf_counter() - ts   # the depth loop only
+            pts += w.points
+            errs.append(float(np.linalg.norm(img_gpu[i] - img_ref) / np.linalg.norm(img_ref)))
+        line["cpu_baseline"] = {"value": pts / secs, "unit": "point*freq/s", "cores": O.max_threads(),
+                                "kind": "oracle", "sample": f"the 2 smallest lines ({pts} points x frequencies), "
+                                "FP64 depth loop", "seconds": secs}
+        line["parity"] = {"image_rel_l2_sampled_lines": errs}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 # ------------------------------------------------------------------ GPU leg
 def run_native(args, w):
     import torch
@@ -473,7 +692,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="layered_lens_2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="layered_lens_2048", choices=sorted(WORKLOADS) + [BATCH_NAME])
     ap.add_argument("--mode", type=int, default=0, help="0 auto, 1 persistent, 2 per-depth")
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--groups", type=int, default=0)
@@ -483,6 +702,12 @@ def main(argv=None):
     ap.add_argument("--train-steps", type=int, default=100000, help="Adam steps of the operator network")
     ap.add_argument("--ref-freqs", type=int, default=24, help="frequencies per oracle step (reference arm)")
     args = ap.parse_args(argv)
+    if args.workload == BATCH_NAME:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the "
+                              "single-line workloads"}), flush=True)
+            return 0
+        return run_batch(args)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -306,6 +306,71 @@ int fxmig_mlp_migrate(const fxmig_desc *d, void *slab, const float *vel, const f
                       float *partials, int nparts, int z_begin, int z_end, void *ws, size_t ws_bytes,
                       void *stream);
 
+/* ------------------------------------------------------------------------
+ * Many independent lines in one launch.  The paper migrates one 2-D line;
+ * a survey has many, of uneven size.  fxmig_migrate_batch runs the depth
+ * loop of Algorithm 1 (as fxmig_migrate, persistent form, FP32) for up to
+ * FXMIG_BATCH_MAX_LINES lines, each with its own descriptor (nx, nz, band,
+ * L), velocity, table and wavefield, in ONE kernel launch: every (line,
+ * frequency group) is a work item, clusters of CTAs take items from a device
+ * queue, largest first, and each runs its item's whole depth loop.  The call
+ * enqueues no host copies and no synchronisation, so it can be captured into
+ * a CUDA graph.
+ * ------------------------------------------------------------------------ */
+#define FXMIG_BATCH_MAX_LINES 128
+
+/* One line of a batch.  slab, vel, table, partials as for fxmig_migrate
+ * (device pointers; partials holds the line's count of [nz][nx] images from
+ * fxmig_batch_num_partials); depth rows [z_begin, z_end). */
+typedef struct fxmig_line {
+    fxmig_desc d;
+    void *slab;
+    const float *vel;
+    const void *table;
+    float *partials;
+    int z_begin, z_end;
+} fxmig_line;
+
+/* Launch choices of a batch: cluster = CTAs per frequency group (1, 2, 4, 8;
+ * 0 = 2); lines_cap = most frequency lines per group (0 = as many as fit in
+ * shared memory). */
+typedef struct fxmig_batch_plan {
+    int cluster, lines_cap;
+} fxmig_batch_plan;
+
+/* Device workspace of fxmig_migrate_batch (autotune = 0) or of
+ * fxmig_batch_autotune (autotune = 1: adds scratch copies of every wavefield
+ * and partial rows for the tuning depth range); 0 for invalid lines. */
+size_t fxmig_batch_workspace_bytes(const fxmig_line *lines, int n, int autotune);
+
+/* Partial images that fxmig_migrate_batch writes for each line under plan
+ * (NULL = defaults): nparts[i] for lines[i].  Reads only the descriptors
+ * (the pointers may still be NULL).  A line's frequencies are split into
+ * groups that fit one CTA, and its groups into nparts[i] streams (about four
+ * streams per cluster over the batch, in proportion to each line's work);
+ * each stream sums its groups' image rows, in a fixed order, into one partial
+ * image.  Errors: FXMIG_EINVAL. */
+int fxmig_batch_num_partials(const fxmig_line *lines, int n, const fxmig_batch_plan *plan, int *nparts);
+
+/* Autotuner: times the batch kernel for cluster sizes 1, 2, 4, 8 and lines
+ * caps (all that fit, half of that) on scratch copies of the wavefields over
+ * the first eighth of every line's depth rows (at least 8, so the work items
+ * keep their proportions), and returns the fastest choice in *plan (and its
+ * time in *best_ms, may be NULL).  Leaves the lines' slabs and partials
+ * untouched.  Synchronises the stream.
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC (ws_bytes < fxmig_batch_workspace_bytes(lines, n, 1)),
+ * FXMIG_ECUDA. */
+int fxmig_batch_autotune(const fxmig_line *lines, int n, fxmig_batch_plan *plan, float *best_ms,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* The batch: every line migrated as by fxmig_migrate over its [z_begin,
+ * z_end), with the plan's cluster size and lines per group.  ws: at least
+ * fxmig_batch_workspace_bytes(lines, n, 0) bytes, 256-byte aligned; its
+ * status word is cleared first (fxmig_check(ws) reports device conditions).
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA. */
+int fxmig_migrate_batch(const fxmig_line *lines, int n, const fxmig_batch_plan *plan, void *ws,
+                        size_t ws_bytes, void *stream);
+
 /* Waits for `stream`, then reads and returns the device status word in `ws`
  * (FXMIG_OK, FXMIG_EVELOCITY or FXMIG_ETIMEOUT); FXMIG_ECUDA if the stream
  * reports a CUDA error; FXMIG_EINVAL for a NULL ws. */

@@ -29,6 +29,8 @@ __all__ = [
     "fxmig_check", "fxmig_migrate_noalloc", "desc_for", "migrate_section",
     "fxmig_mlp_param_count", "fxmig_mlp_train_ws_bytes", "fxmig_design_at", "fxmig_mlp_train",
     "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials", "fxmig_mlp_migrate",
+    "Line", "BatchPlan", "line_of", "fxmig_batch_workspace_bytes", "fxmig_batch_num_partials",
+    "fxmig_batch_autotune", "fxmig_migrate_batch",
 ]
 
 FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
@@ -59,6 +61,17 @@ class Desc(ctypes.Structure):
 
     def __repr__(self):
         return "Desc(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
+
+
+class Line(ctypes.Structure):
+    """Mirror of ``fxmig_line`` (one line of a batch; device pointers)."""
+    _fields_ = [("d", Desc), ("slab", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("table", ctypes.c_void_p),
+                ("partials", ctypes.c_void_p), ("z_begin", ctypes.c_int), ("z_end", ctypes.c_int)]
+
+
+class BatchPlan(ctypes.Structure):
+    """Mirror of ``fxmig_batch_plan`` (zeros = defaults)."""
+    _fields_ = [("cluster", ctypes.c_int), ("lines_cap", ctypes.c_int)]
 
 
 class Launch(ctypes.Structure):
@@ -101,10 +114,17 @@ def lib():
         L.fxmig_mlp_taps.argtypes = [pd, vp, vp, i, vp, vp]
         L.fxmig_mlp_num_partials.argtypes = [pd]
         L.fxmig_mlp_migrate.argtypes = [pd, vp, vp, vp, vp, i, i, i, vp, sz, vp]
+        pln, pbp = ctypes.POINTER(Line), ctypes.POINTER(BatchPlan)
+        L.fxmig_batch_workspace_bytes.argtypes = [pln, i, i]
+        L.fxmig_batch_workspace_bytes.restype = sz
+        L.fxmig_batch_num_partials.argtypes = [pln, i, pbp, ctypes.POINTER(ctypes.c_int)]
+        L.fxmig_batch_autotune.argtypes = [pln, i, pbp, ctypes.POINTER(ctypes.c_float), vp, sz, vp]
+        L.fxmig_migrate_batch.argtypes = [pln, i, pbp, vp, sz, vp]
         for f in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex",
                   "fxmig_image", "fxmig_check", "fxmig_mlp_param_count", "fxmig_design_at",
                   "fxmig_mlp_train", "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials",
-                  "fxmig_mlp_migrate"):
+                  "fxmig_mlp_migrate", "fxmig_batch_num_partials", "fxmig_batch_autotune",
+                  "fxmig_migrate_batch"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -329,6 +349,52 @@ def fxmig_mlp_migrate(d: Desc, slab, vel, params, partials, z_begin, z_end, ws, 
     rc = lib().fxmig_mlp_migrate(ctypes.byref(d), bp, vp, mp, pp, int(nparts), int(z_begin), int(z_end), wp,
                                  ws.numel() * ws.element_size(), _stream(stream))
     _check(rc, "fxmig_mlp_migrate")
+
+
+# ------------------------------------------------------------ batches of lines
+def line_of(d: Desc, slab, vel, table, partials, z_begin=0, z_end=None) -> Line:
+    """A ``fxmig_line`` for torch tensors (device, contiguous); keep the
+    tensors alive while the line is used."""
+    torch = _torch()
+    return Line(d=d, slab=_dev_ptr(slab, "slab", torch.float32, 2 * d.nw * d.nx, complex_ok=True),
+                vel=_dev_ptr(vel, "vel", torch.float32, d.nz * d.nx),
+                table=_dev_ptr(table, "table", torch.float32, 2 * d.nk * (d.L + 1), complex_ok=True),
+                partials=_dev_ptr(partials, "partials", torch.float32),
+                z_begin=int(z_begin), z_end=int(d.nz if z_end is None else z_end))
+
+
+def _lines_array(lines):
+    arr = (Line * len(lines))(*lines)
+    return arr, len(lines)
+
+
+def fxmig_batch_workspace_bytes(lines, autotune: bool = False) -> int:
+    arr, n = _lines_array(lines)
+    return int(lib().fxmig_batch_workspace_bytes(arr, n, 1 if autotune else 0))
+
+
+def fxmig_batch_num_partials(lines, plan: BatchPlan | None = None) -> list:
+    """Partial images of every line (only the descriptors are read)."""
+    arr, n = _lines_array(lines)
+    out = (ctypes.c_int * n)()
+    _check(lib().fxmig_batch_num_partials(arr, n, ctypes.byref(plan) if plan else None, out),
+           "fxmig_batch_num_partials")
+    return list(out)
+
+
+def fxmig_batch_autotune(lines, ws, stream=None):
+    """Returns (BatchPlan, best time in ms over the tuning depth rows)."""
+    arr, n = _lines_array(lines)
+    plan, ms = BatchPlan(), ctypes.c_float(0.0)
+    _check(lib().fxmig_batch_autotune(arr, n, ctypes.byref(plan), ctypes.byref(ms), _dev_ptr(ws, "ws"),
+                                      ws.numel() * ws.element_size(), _stream(stream)), "fxmig_batch_autotune")
+    return plan, float(ms.value)
+
+
+def fxmig_migrate_batch(lines, plan: BatchPlan | None, ws, stream=None) -> None:
+    arr, n = _lines_array(lines)
+    _check(lib().fxmig_migrate_batch(arr, n, ctypes.byref(plan) if plan else None, _dev_ptr(ws, "ws"),
+                                     ws.numel() * ws.element_size(), _stream(stream)), "fxmig_migrate_batch")
 
 
 # ------------------------------------------------------------------ conveniences

@@ -5,12 +5,37 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fxmig_internal.cuh"
 #include "mlp_internal.cuh"
 
 using namespace fxmig_impl;
 
 namespace fxmig_impl {
+
+cudaError_t kernel_smem_attr(const void* func, size_t bytes, bool nonportable_cluster) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, std::pair<size_t, bool>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto& st = done[{dev, func}];
+    if (bytes > st.first) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        st.first = bytes;
+    }
+    if (nonportable_cluster && !st.second) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        st.second = true;
+    }
+    return cudaSuccess;
+}
 
 bool desc_valid(const fxmig_desc* d) {
     if (!d) return false;
@@ -198,6 +223,47 @@ int fxmig_mlp_migrate(const fxmig_desc* d, void* slab, const float* vel, const f
     const cudaError_t e = launch_mlp_migrate(d, plan, slab, vel, params, partials, z_begin, z_end, ws,
                                              static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_mlp_migrate");
+}
+
+size_t fxmig_batch_workspace_bytes(const fxmig_line* lines, int n, int autotune) {
+    if (!batch_lines_valid(lines, n)) return 0;
+    return batch_ws_bytes(lines, n, autotune != 0);
+}
+
+int fxmig_batch_num_partials(const fxmig_line* lines, int n, const fxmig_batch_plan* plan, int* nparts) {
+    if (!batch_descs_valid(lines, n) || !nparts) return FXMIG_EINVAL;
+    return batch_num_partials(lines, n, plan, nparts);
+}
+
+static bool batch_plan_ok(const fxmig_batch_plan* p) {
+    return !p || ((p->cluster == 0 || p->cluster == 1 || p->cluster == 2 || p->cluster == 4 || p->cluster == 8) &&
+                  p->lines_cap >= 0);
+}
+
+int fxmig_batch_autotune(const fxmig_line* lines, int n, fxmig_batch_plan* plan, float* best_ms, void* ws,
+                         size_t ws_bytes, void* stream) {
+    if (!batch_lines_valid(lines, n) || !plan || !ws || !aligned(ws, 256)) return FXMIG_EINVAL;
+    if (ws_bytes < batch_ws_bytes(lines, n, true)) return FXMIG_ENOSPC;
+    const int rc = batch_autotune(lines, n, plan, ws, static_cast<cudaStream_t>(stream), best_ms);
+    if (rc == FXMIG_ECUDA) return cuda_fail(cudaGetLastError(), "fxmig_batch_autotune");
+    return rc;
+}
+
+int fxmig_migrate_batch(const fxmig_line* lines, int n, const fxmig_batch_plan* plan, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!batch_lines_valid(lines, n) || !batch_plan_ok(plan) || !ws || !aligned(ws, 256)) return FXMIG_EINVAL;
+    if (ws_bytes < batch_ws_bytes(lines, n, false)) return FXMIG_ENOSPC;
+    fxmig_batch_plan p = {2, 0};
+    if (plan) {
+        p = *plan;
+        if (p.cluster == 0) p.cluster = 2;
+    }
+    {  // every line must be plannable (shared memory, cluster width)
+        int np[FXMIG_BATCH_MAX_LINES];
+        if (batch_num_partials(lines, n, &p, np) != FXMIG_OK) return FXMIG_EINVAL;
+    }
+    const cudaError_t e = launch_batch(lines, n, p, ws, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate_batch");
 }
 
 int fxmig_check(const void* ws, void* stream) {

@@ -131,7 +131,7 @@ cudaError_t launch_design(const fxmig_desc* d, const double* kvals, int n, void*
     const double dk = d->nk > 1 ? d->k_max / (double)(d->nk - 1) : 0.0;
     const double sin_theta = sin(d->theta_max_deg * (3.14159265358979323846 / 180.0));
     const size_t smem = ((size_t)M * n1 + 3 * (size_t)M + (size_t)n1 * n1 + 2 * (size_t)n1 + 256) * 8;
-    cudaError_t e = cudaFuncSetAttribute(k_design, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k_design, smem);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     k_design<<<n, 256, smem, s>>>(n, dk, kvals, d->dx, d->dz, d->L, sin_theta, M, static_cast<float2*>(table),

@@ -161,6 +161,17 @@ __device__ __forceinline__ void st_cluster_v2(uint32_t addr, float2 v) {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// ------------------------------------------------------------ kernel attributes
+// Dynamic shared memory limit (and, for cluster kernels, the non-portable
+// cluster size permission) of a kernel on the current device, set once and
+// raised only when a launch needs more: a launch repeated inside a stream
+// capture then makes no attribute call.
+cudaError_t kernel_smem_attr(const void* func, size_t bytes, bool nonportable_cluster);
+template <class F>
+inline cudaError_t ensure_smem(F* func, size_t bytes, bool nonportable_cluster = false) {
+    return kernel_smem_attr(reinterpret_cast<const void*>(func), bytes, nonportable_cluster);
+}
+
 // ------------------------------------------------------------ host interfaces
 struct MigratePlan {
     int mode;      // FXMIG_MODE_PERSISTENT or FXMIG_MODE_PER_DEPTH
@@ -199,6 +210,14 @@ struct MigrateArgs;
 bool rp_compiled(int LT);
 cudaError_t expand_taps_rp(int precision, const float2* table, int nk, int L, int LT, void* taps, cudaStream_t s);
 cudaError_t launch_persistent_rp(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s);
+// many lines in one persistent launch (batch.cu)
+bool batch_descs_valid(const fxmig_line* lines, int n);
+bool batch_lines_valid(const fxmig_line* lines, int n);
+size_t batch_ws_bytes(const fxmig_line* lines, int n, bool scratch);
+int batch_num_partials(const fxmig_line* lines, int n, const fxmig_batch_plan* plan, int* out);
+cudaError_t launch_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, void* ws, cudaStream_t s);
+int batch_autotune(const fxmig_line* lines, int n, fxmig_batch_plan* out, void* ws, cudaStream_t s,
+                   float* best_ms);
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
                          cudaStream_t s);
 

@@ -250,7 +250,7 @@ template <int LT>
 static cudaError_t launch_lt(const MigratePlan& plan, MigrateArgs a, cudaStream_t s, float2* ws_slab) {
     if (plan.mode == FXMIG_MODE_PERSISTENT) return launch_persistent<LT, WsF32, TapF32>(plan, a, s);
     auto kern = k_migrate_step<LT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    cudaError_t e = ensure_smem(kern, plan.smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.nx + kStepTile - 1) / kStepTile, plan.groups);
     float2* bufs[2] = {a.slab, ws_slab};
@@ -288,7 +288,10 @@ cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* s
         e = expand_taps_rp(plan.precision, static_cast<const float2*>(table), d->nk, d->L, LT, taps, s);
     }
     if (e != cudaSuccess) return e;
-    const bool use_slow = precompute_slowness && plan.mode == FXMIG_MODE_PERSISTENT;
+    // precomputed slowness rows are read through the TMA ring only (the depth
+    // loop's 16-byte row loads need the staged copy): with nx not a multiple
+    // of 4 the rows are converted from the velocity in shared memory instead
+    const bool use_slow = precompute_slowness && plan.mode == FXMIG_MODE_PERSISTENT && (d->nx & 3) == 0;
     if (use_slow) {
         // only the rows this call reads
         const size_t n_rows = (size_t)(z_end - z_begin) * d->nx;
@@ -301,7 +304,7 @@ cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* s
         if (e != cudaSuccess) return e;
     }
     MigrateArgs a = {};
-    a.nx = d->nx; a.nz = d->nz; a.nw = d->nw; a.nk = d->nk;
+    a.nx = d->nx; a.nz = d->nz; a.nw = d->nw; a.nk = d->nk; a.L = d->L;
     a.z_begin = z_begin; a.z_end = z_end; a.i0 = d->i0; a.nt = d->nt;
     a.dt = d->dt;
     a.dk = d->nk > 1 ? d->k_max / (double)(d->nk - 1) : 0.0;

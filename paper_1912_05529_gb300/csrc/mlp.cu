@@ -377,7 +377,7 @@ cudaError_t launch_mlp_train(int L, float* params, float* m, float* v, int step0
     float* partial = static_cast<float*>(ws);
     float* lossp = partial + (size_t)ctas * P;
     const size_t smem = sizeof(TrainSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k_mlp_grad, smem);
     if (e != cudaSuccess) return e;
     const double inv_kmax = 1.0 / k_max;
     for (int i = 0; i < nsteps; ++i) {
@@ -567,7 +567,7 @@ static int sm_count() {
 
 static cudaError_t launch_infer(const InferArgs& a, long long max_total, cudaStream_t s) {
     const size_t smem = sizeof(WeightSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k_mlp_infer, smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (max_total + 15) / 16;
     long long grid = (tiles + kInferWarps - 1) / kInferWarps;

@@ -269,7 +269,7 @@ static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& 
                                      cudaStream_t s) {
     const size_t smem = (size_t)(kPairTile + kPairWarps * kPairTile) * 4 +
                         (size_t)kPairWarps * (((kPairTile + 2 * LT + 7) >> 3) * 10) * 8;
-    cudaError_t e = cudaFuncSetAttribute(k_step_pairs<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k_step_pairs<LT>, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((d->nx + kPairTile - 1) / kPairTile, plan.groups);
     a.z0 = z0;
@@ -294,7 +294,7 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
     const int nxp = next_pow2(d->nx);
     const int nth = std::min(kUniqueThreads, nxp);
     const size_t usmem = (size_t)nxp * 8;
-    e = cudaFuncSetAttribute(k_row_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+    e = ensure_smem(k_row_unique, usmem);
     if (e != cudaSuccess) return e;
     k_row_unique<<<z_end - z_begin, nth, usmem, s>>>(vel, d->nx, nxp, z_begin, w.uval, w.uidx, w.cnt, w.status);
     e = cudaGetLastError();

@@ -23,7 +23,7 @@
 namespace fxmig_impl {
 
 struct MigrateArgs {
-    int nx, nz, nw, nk, z_begin, z_end, i0, nt;
+    int nx, nz, nw, nk, z_begin, z_end, i0, nt, L;
     double dt, dk;
     float2* slab;           // [nw][nx]
     const float* vel;       // [nz][nx]
@@ -34,6 +34,8 @@ struct MigrateArgs {
     int W, C, G, lines, tma_ok;
     int cwarps, ewarps;     // persistent: interior compute warps, edge warps
     int img;                // persistent: imaging buffer in shared memory (persistent_layout)
+    int part_fixed, part;   // partial image written: group g's own (0) or number `part` (1)
+    int accumulate;         // add the group's rows to the partial image instead of storing them
     // per-depth form
     const float2* in;
     float2* out;
@@ -190,11 +192,19 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
     }
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
+// The whole depth loop of frequency group g of problem a, on the CTAs of one
+// cluster (all of them call it with the same a and g).  smem is the CTA's
+// dynamic shared memory (persistent_layout).  On return every mbarrier used
+// is invalidated and no copy or remote store is in flight, so the memory can
+// hold the next group.
 template <int LT, class WS, class TP>
-__global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
+__device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
     const typename TP::E* __restrict__ taps = static_cast<const typename TP::E*>(a.taps);
-    extern __shared__ __align__(128) unsigned char smem[];
     const int W = a.W, m = a.lines, C = a.C;
     const int SP = seg_phys_len(W, LT);
     const int NC = W >> 3;
@@ -207,7 +217,6 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     T* wave = reinterpret_cast<T*>(smem + L.wave);
 
     const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
-    const int g = blockIdx.x / C;
     const int l_begin = (int)(((long long)g * a.nw) / a.G);
     const int mg = (int)(((long long)(g + 1) * a.nw) / a.G) - l_begin;
     const int x0 = rank * W;
@@ -254,8 +263,10 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
         if (!mbar_wait_bounded(&mbar[b], (uint32_t)(((z - a.z_begin) / kRowSlots) & 1), kWaitPolls))
             atomicOr(a.status, kStatusTimeout);
     };
+    // the row the items read (16-byte loads): the staged slowness row, or the
+    // converted row in sbuf (precomputed slowness is only passed with tma_ok)
     auto srow_of = [&](int z) -> const float* {
-        if (a.slow) return a.tma_ok ? (vbuf + (z % kRowSlots) * W) : (a.slow + (size_t)z * a.nx + x0);
+        if (a.slow) return vbuf + (z % kRowSlots) * W;
         return sbuf + (z & 1) * W;
     };
     // s = fl32(1/v) for the CTA's x segment (only without precomputed slowness)
@@ -279,8 +290,9 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     // depth z: from the imaging buffer after the step barrier, or (no buffer)
     // from the step's input wavefield, which nobody writes during the step,
     // before the barrier
+    const int part = a.part_fixed ? a.part : g;
     auto reduce_image_row = [&](int z, const T* cur) {
-        float* dst = a.partials + ((size_t)g * a.nz + z) * a.nx + x0;
+        float* dst = a.partials + ((size_t)part * a.nz + z) * a.nx + x0;
         if (img) {
             const float* src = img + (size_t)(z & 1) * m * W;
             for (int x = tid * 4; x < wv; x += nthr * 4) {
@@ -290,17 +302,21 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
                     acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
                 }
                 if (x + 4 <= wv && (a.nx & 3) == 0) {
+                    if (a.accumulate) {
+                        const float4 o = *reinterpret_cast<const float4*>(dst + x);
+                        acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+                    }
                     *reinterpret_cast<float4*>(dst + x) = acc;
                 } else {
                     const float t[4] = {acc.x, acc.y, acc.z, acc.w};
-                    for (int i = 0; i < 4 && x + i < wv; ++i) dst[x + i] = t[i];
+                    for (int i = 0; i < 4 && x + i < wv; ++i) dst[x + i] = a.accumulate ? dst[x + i] + t[i] : t[i];
                 }
             }
         } else {
             for (int x = tid; x < wv; x += nthr) {
                 float acc = 0.f;
                 for (int s = 0; s < mg; ++s) acc += WS::to_f2(cur[(size_t)s * SP + phys(x + LT)]).x;
-                dst[x] = acc;
+                dst[x] = a.accumulate ? dst[x] + acc : acc;
             }
         }
     };
@@ -400,6 +416,8 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     // nothing is pushed at the last step and every earlier push has been
     // waited for; the final barrier keeps the CTAs' exits ordered
     if (C > 1) cluster_sync_all(); else __syncthreads();
+    if (tid == 0)
+        for (int b = 0; b < kRowSlots + 4; ++b) mbar_inval(&mbar[b]);
 
     const T* fin = wave + (size_t)((a.z_end - a.z_begin) & 1) * m * SP;
     for (int s = 0; s < mg; ++s) {
@@ -408,17 +426,21 @@ __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent
     }
 }
 
+// One launch of the persistent form: cluster blockIdx.x / C runs group
+// blockIdx.x / C of the problem.
+template <int LT, class WS, class TP>
+__global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    run_group<LT, WS, TP>(a, (int)(blockIdx.x / a.C), smem);
+}
+
 
 // One launch of the persistent form for compiled LT and storage policies.
 template <int LT, class WS, class TP>
 cudaError_t launch_persistent(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
     auto kern = k_migrate_persistent<LT, WS, TP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    cudaError_t e = ensure_smem(kern, plan.smem, plan.cluster > 1);
     if (e != cudaSuccess) return e;
-    if (plan.cluster > 1) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(plan.groups * plan.cluster);
     cfg.blockDim = dim3(plan.warps * 32);

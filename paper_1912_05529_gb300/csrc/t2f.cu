@@ -176,7 +176,7 @@ cudaError_t launch_t2f(const fxmig_desc* d, const float* section, void* slab, vo
     k_twiddles<<<(d->nt + 255) / 256, 256, 0, s>>>(d->nt, tw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_t2f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(k_t2f, smem);
     if (e != cudaSuccess) return e;
     const int grid = (pairs + T - 1) / T;
     k_t2f<<<grid, 256, smem, s>>>(a);

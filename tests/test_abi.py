@@ -167,3 +167,28 @@ def test_learned_operator_entry_points_reject_bad_arguments(fx):
     assert need > 0
     assert lib.fxmig_mlp_migrate(ctypes.byref(d), ok, ok, None, ok, 64, 0, 5, ok, need, None) == fx.FXMIG_EINVAL
     assert lib.fxmig_mlp_migrate(ctypes.byref(d), ok, ok, ok, ok, 64, 0, 5, ok, need - 1, None) == fx.FXMIG_ENOSPC
+
+
+def test_batch_entry_points_reject_bad_arguments(fx):
+    lib = fx.lib()
+    d = _desc(fx)
+    ok = ctypes.c_void_p(1 << 20)
+    good = fx.Line(d=d, slab=ok, vel=ok, table=ok, partials=ok, z_begin=0, z_end=d.nz)
+    arr = (fx.Line * 2)(good, good)
+    out = (ctypes.c_int * 2)()
+    assert lib.fxmig_batch_num_partials(arr, 2, None, out) == fx.FXMIG_OK and min(out) >= 1
+    assert lib.fxmig_batch_num_partials(arr, 0, None, out) == fx.FXMIG_EINVAL
+    bad_plan = fx.BatchPlan(cluster=3)
+    assert lib.fxmig_batch_num_partials(arr, 2, ctypes.byref(bad_plan), out) == fx.FXMIG_EINVAL
+    need = lib.fxmig_batch_workspace_bytes(arr, 2, 0)
+    assert need > 0 and lib.fxmig_batch_workspace_bytes(arr, 2, 1) > need
+    assert lib.fxmig_migrate_batch(arr, 2, None, None, need, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_migrate_batch(arr, 2, None, ok, need - 1, None) == fx.FXMIG_ENOSPC
+    assert lib.fxmig_migrate_batch(arr, 2, ctypes.byref(bad_plan), ok, need, None) == fx.FXMIG_EINVAL
+    many = (fx.Line * 129)(*([good] * 129))
+    assert lib.fxmig_batch_workspace_bytes(many, 129, 0) == 0
+    nulled = fx.Line(d=d, slab=ok, vel=None, table=ok, partials=ok, z_begin=0, z_end=d.nz)
+    arr2 = (fx.Line * 1)(nulled)
+    assert lib.fxmig_migrate_batch(arr2, 1, None, ok, need, None) == fx.FXMIG_EINVAL
+    plan = fx.BatchPlan()
+    assert lib.fxmig_batch_autotune(arr, 2, ctypes.byref(plan), None, ok, need, None) == fx.FXMIG_ENOSPC

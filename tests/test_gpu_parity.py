@@ -158,3 +158,23 @@ def test_diffractor_end_to_end(fx):
     assert rel_l2(img, ref_img) < TOL_IMAGE
     iz, ix = np.unravel_index(np.argmax(np.abs(img)), img.shape)
     assert abs(ix - 64) <= 1 and abs(iz - 60) <= 1
+
+
+@pytest.mark.parametrize("nx", [333, 514, 1021])
+@pytest.mark.parametrize("launch", [None, dict(mode=1, cluster=2), dict(mode=1, cluster=4, precision=3),
+                                    dict(mode=2)])
+def test_migrate_widths_not_multiple_of_four(fx, nx, launch):
+    # rows of nx % 4 != 0 floats are not 16-byte aligned in device memory:
+    # the persistent form then converts velocity rows in shared memory
+    w = small_layered(nx=nx, nz=30, name=f"layered_{nx}")
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    d = desc_of(fx, w, pr["k_max"])
+    lc = fx.Launch(**launch) if launch else None
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, lc)
+    P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if not (launch and launch.get("precision")) else (1e-2, 1e-2)
+    assert rel_l2(slabs[-1], P_ref) < tol_s
+    assert rel_l2(image, img_ref) < tol_i
