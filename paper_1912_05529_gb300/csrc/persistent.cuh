@@ -82,10 +82,10 @@ template <int LT, class WS>
 __device__ __forceinline__ void push_halo(const SegCtx& g, size_t nxt_off, int s, int x, u64 v, int pb) {
     if (g.has_left && x < LT)
         WS::st_async(g.nb_left + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(g.W + LT + x)) * WS::kBytes), v,
-                     g.bar_left[pb]);
+                     pb ? g.bar_left[1] : g.bar_left[0]);
     if (g.has_right && x >= g.W - LT)
         WS::st_async(g.nb_right + (uint32_t)((nxt_off + (size_t)s * g.SP + phys(x - g.W + LT)) * WS::kBytes), v,
-                     g.bar_right[pb]);
+                     pb ? g.bar_right[1] : g.bar_right[0]);
 }
 
 // Write one output (local position x of line s) to the next buffer and, when
@@ -308,8 +308,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                     }
                     *reinterpret_cast<float4*>(dst + x) = acc;
                 } else {
-                    const float t[4] = {acc.x, acc.y, acc.z, acc.w};
-                    for (int i = 0; i < 4 && x + i < wv; ++i) dst[x + i] = a.accumulate ? dst[x + i] + t[i] : t[i];
+                    for (int i = 0; i < 4 && x + i < wv; ++i) {
+                        const float t = i == 0 ? acc.x : i == 1 ? acc.y : i == 2 ? acc.z : acc.w;
+                        dst[x + i] = a.accumulate ? dst[x + i] + t : t;
+                    }
                 }
             }
         } else {
@@ -353,6 +355,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     // step's input wavefield.
     const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
     const int n_items = mg * NC;
+    // item / NC by a multiply-high with m = ceil(2^32 / NC): exact while
+    // item * NC < 2^32, which n_items * NC < 2^32 guarantees
+    const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
+    const bool magic_ok = (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
@@ -378,19 +384,28 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         for (int base = warp * 32; base < n_items; base += nwarps * 32) {
             const int item = base + lane;
             int s = 0, xl0 = 0;
-            bool work = false, edge = false;
+            bool work = false, edge = false, need_l = false, need_r = false;
             if (item < n_items) {
-                s = item / NC;
+                s = magic_ok ? (int)__umulhi((uint32_t)item, nc_magic) : item / NC;
                 const int c = item - s * NC;
                 xl0 = c << 3;
                 work = xl0 < wv;
                 edge = (C > 1) && (c < E || c >= NC - E);
+                // Chunks c < E read the left halo and push to the left
+                // neighbour, chunks c >= NC - E the right ones (both also when
+                // the chunk lies beyond the line end and only pushes zeros).
+                // Waiting for the neighbour's previous step on that side is
+                // what keeps the two CTAs within one step of each other, so a
+                // pusher waits even when it reads nothing.
+                need_l = sc.has_left && c < E;
+                need_r = sc.has_right && c >= NC - E;
             }
-            if (halo_wait && __any_sync(0xffffffffu, edge)) {
+            if (halo_wait) {
                 // the neighbours' outputs of step z-1 have landed in cur's halo
+                const bool wl = __any_sync(0xffffffffu, need_l), wr = __any_sync(0xffffffffu, need_r);
                 bool ok = true;
-                if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
-                if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                if (wl) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                if (wr) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             uint32_t mask = 0;
