@@ -50,20 +50,18 @@ __device__ __forceinline__ void fir8_ptrs(const float2* __restrict__ wbase, cons
     u64 A[8], B[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        u64 hr, hi;
-        ldg_nc_v2(tp[r], hr, hi);
-        A[r] = f2_mul(hr, w[LT + r]);
-        B[r] = f2_mul(hi, w[LT + r]);
+        const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(tp[r]));
+        A[r] = f2_mul(h.x, w[LT + r]);
+        B[r] = f2_mul(h.y, w[LT + r]);
     }
 #pragma unroll
     for (int n = 1; n <= LT; ++n) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            u64 hr, hi;
-            ldg_nc_v2(tp[r] + n, hr, hi);
+            const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(tp[r] + n));
             const u64 t = f2_add(w[LT + r - n], w[LT + r + n]);
-            A[r] = f2_fma(hr, t, A[r]);
-            B[r] = f2_fma(hi, t, B[r]);
+            A[r] = f2_fma(h.x, t, A[r]);
+            B[r] = f2_fma(h.y, t, B[r]);
         }
     }
 #pragma unroll
@@ -175,7 +173,12 @@ typedef WsHalf<H2BF16> WsBF16;
 // the packed pairs (hr, hr) and (hi, hi).
 struct TapF32 {  // (hr, hr, hi, hi) in FP32, 16 bytes
     typedef float4 E;
-    __device__ static __forceinline__ void ld(const E* p, u64& hr, u64& hi) { ldg_nc_v2(p, hr, hi); }
+    // read-only path; a plain load so that tap offsets fold into the address
+    __device__ static __forceinline__ void ld(const E* p, u64& hr, u64& hi) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        hr = v.x;
+        hi = v.y;
+    }
 };
 // 16-bit taps: (hr, hi) rounded to the half type (4 bytes), or with kSplit
 // the rounded pair and the rounded remainder, h = hi_part + lo_part (8 bytes).

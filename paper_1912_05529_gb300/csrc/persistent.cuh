@@ -327,6 +327,12 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         for (int zz = a.z_begin; zz < min(a.z_end, a.z_begin + kRowAhead); ++zz) issue_row(zz);
     wait_row(a.z_begin);
     convert_row(a.z_begin);
+    // From here on one thread waits for each staged row, one step before the
+    // row is read, and the step barrier publishes it to the CTA: row z + 1
+    // (slowness rows, read by the items of step z + 1) or row z + 2 (velocity
+    // rows, converted during step z + 1) is waited for before the barrier
+    // that ends step z.
+    if (!a.slow && tid == 0 && a.z_begin + 1 < a.z_end) wait_row(a.z_begin + 1);
     // every CTA of the cluster has zeroed its buffers before any halo push
     if (C > 1) cluster_sync_all(); else __syncthreads();
 
@@ -359,6 +365,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     // item * NC < 2^32, which n_items * NC < 2^32 guarantees
     const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
     const bool magic_ok = (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
+    const bool spread = (NC & 31) == 0;  // lines of whole warps of items
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
@@ -379,7 +386,6 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes);
             }
         }
-        if (a.slow && z > a.z_begin) wait_row(z);  // (converted rows were synchronised)
 
         for (int base = warp * 32; base < n_items; base += nwarps * 32) {
             const int item = base + lane;
@@ -387,7 +393,14 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             bool work = false, edge = false, need_l = false, need_r = false;
             if (item < n_items) {
                 s = magic_ok ? (int)__umulhi((uint32_t)item, nc_magic) : item / NC;
-                const int c = item - s * NC;
+                const int j = item - s * NC;
+                // spread a warp's 32 items over the line: item j = 32a + 8q + r
+                // takes chunk 8 (q NC/32 + a) + r, so each warp covers four
+                // blocks of 8 chunks a quarter of the line apart (velocity
+                // changes, which cost extra work, are shared between warps);
+                // a quarter-warp keeps 8 consecutive chunks (conflict-free
+                // window loads)
+                const int c = spread ? ((((j >> 3) & 3) * (NC >> 5) + (j >> 5)) << 3) + (j & 7) : j;
                 xl0 = c << 3;
                 work = xl0 < wv;
                 edge = (C > 1) && (c < E || c >= NC - E);
@@ -419,10 +432,11 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             if (__any_sync(0xffffffffu, mask != 0u))
                 coop_fixups<LT, WS, TP>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, taps, lane, push, pb);
         }
-        if (!a.slow && z + 1 < a.z_end) {
-            // velocity rows are converted by the whole CTA before the next step
-            wait_row(z + 1);
-            convert_row(z + 1);
+        // velocity rows are converted by the whole CTA one step ahead
+        if (!a.slow && z + 1 < a.z_end) convert_row(z + 1);
+        {
+            const int zw = a.slow ? z + 1 : z + 2;
+            if (tid == 0 && zw < a.z_end) wait_row(zw);
         }
         if (!img) reduce_image_row(z, cur);
         __syncthreads();
