@@ -26,6 +26,8 @@ cudaError_t launch_mlp_block_taps(const fxmig_desc* d, int LT, const float* para
 struct MlpMigratePlan {
     int LT, groups, zc;  // compiled half-length, frequency tiles, rows per operator block
     int nparts;
+    int persistent;      // depth steps by the persistent form (else one launch per row)
+    MigratePlan pplan;   // its plan
 };
 int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p);
 size_t mlp_migrate_ws_bytes(const fxmig_desc* d);

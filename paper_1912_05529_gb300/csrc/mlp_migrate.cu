@@ -9,9 +9,13 @@
 //   k_pair_offsets  first (frequency, value) pair of every row (prefix sums
 //                   of nw * count);
 //   per block of Zc rows: the network writes the operators of all pairs of
-//   the block (k_mlp_infer), then one Eq. 1 step per row streams the
-//   wavefield through L2/HBM (k_step_pairs, 256 outputs of a frequency tile
-//   per CTA, output x of line w using the operator of pair (w, uidx[z][x])).
+//   the block (k_mlp_infer), then the block's depth steps run in the
+//   persistent form (the frequency lines stay in shared memory for the
+//   block's rows; the staged rows hold every point's pair index instead of
+//   its slowness), or, when rows cannot be staged by TMA (nx not a multiple
+//   of 4), one Eq. 1 launch per row streams the wavefield through L2/HBM
+//   (k_step_pairs, 256 outputs of a frequency tile per CTA, output x of
+//   line w using the operator of pair (w, uidx[z][x])).
 // Every launch reads its counts from device memory: no host synchronisation.
 #include <float.h>
 
@@ -19,6 +23,7 @@
 
 #include "fir.cuh"
 #include "mlp_internal.cuh"
+#include "persistent.cuh"
 
 namespace fxmig_impl {
 
@@ -213,12 +218,19 @@ int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p) {
     const int LT = compiled_half_length(d->L);
     if (LT < 0) return FXMIG_EINVAL;
     p->LT = LT;
-    p->groups = std::max(1, std::min(d->nw, 16));
-    p->nparts = p->groups;
+    // persistent form when pair-index rows can be staged by TMA
+    p->persistent = 0;
+    if ((d->nx & 3) == 0) {
+        fxmig_launch lp = {};
+        lp.mode = FXMIG_MODE_PERSISTENT;
+        if (plan_migrate(d, &lp, &p->pplan) == FXMIG_OK) p->persistent = 1;
+    }
+    p->groups = p->persistent ? p->pplan.groups : std::max(1, std::min(d->nw, 16));
+    p->nparts = p->persistent ? p->pplan.nparts : p->groups;
     // rows per operator block: worst-case operator storage (every point of a
-    // row distinct) of about 1 GiB at most
+    // row distinct) of about 2 GiB at most
     const double row_bytes = (double)d->nw * d->nx * (LT + 1) * 16.0;
-    p->zc = (int)std::max(1.0, std::min(16.0, std::floor((double)(1u << 30) / row_bytes)));
+    p->zc = (int)std::max(1.0, std::min(64.0, std::floor(2.0 * (double)(1u << 30) / row_bytes)));
     return FXMIG_OK;
 }
 
@@ -314,10 +326,41 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
     a.partials = partials;
     float2* bufs[2] = {static_cast<float2*>(slab), w.slab2};
     int parity = 0;
+    MigrateArgs pa = {};
+    if (plan.persistent) {
+        pa.nx = d->nx; pa.nz = d->nz; pa.nw = d->nw; pa.nk = d->nk; pa.i0 = d->i0; pa.nt = d->nt; pa.L = d->L;
+        pa.dt = d->dt;
+        pa.slab = static_cast<float2*>(slab);
+        pa.vel = vel;
+        pa.slow = reinterpret_cast<const float*>(w.uidx);  // pair indices, staged like slowness rows
+        pa.taps = w.taps;
+        pa.partials = partials;
+        pa.status = w.status;
+        pa.W = plan.pplan.W; pa.C = plan.pplan.cluster; pa.G = plan.pplan.groups; pa.lines = plan.pplan.lines;
+        pa.cwarps = plan.pplan.cwarps;
+        pa.img = plan.pplan.img;
+        pa.tma_ok = 1;  // nx % 4 == 0 and the workspace arrays are 256-byte aligned
+        pa.pair_cnt = w.cnt;
+        pa.pair_base = w.base;
+    }
     for (int z0 = z_begin; z0 < z_end; z0 += plan.zc) {
         const int z1 = std::min(z_end, z0 + plan.zc);
         e = launch_mlp_block_taps(d, plan.LT, params, w.uval, w.cnt, w.base, z0, z1, w.taps, s);
         if (e != cudaSuccess) return e;
+        if (plan.persistent) {
+            pa.z_begin = z0;
+            pa.z_end = z1;
+            pa.pair_z0 = z0;
+            switch (plan.LT) {
+                case 4: e = launch_persistent<4, WsF32, TapF32, true>(plan.pplan, pa, s); break;
+                case 8: e = launch_persistent<8, WsF32, TapF32, true>(plan.pplan, pa, s); break;
+                case 12: e = launch_persistent<12, WsF32, TapF32, true>(plan.pplan, pa, s); break;
+                case 16: e = launch_persistent<16, WsF32, TapF32, true>(plan.pplan, pa, s); break;
+                default: e = cudaErrorInvalidValue; break;
+            }
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         switch (plan.LT) {
             case 4: e = launch_pair_steps<4>(d, plan, w, a, z0, z1, bufs, parity, s); break;
             case 8: e = launch_pair_steps<8>(d, plan, w, a, z0, z1, bufs, parity, s); break;

@@ -36,6 +36,12 @@ struct MigrateArgs {
     int img;                // persistent: imaging buffer in shared memory (persistent_layout)
     int part_fixed, part;   // partial image written: group g's own (0) or number `part` (1)
     int accumulate;         // add the group's rows to the partial image instead of storing them
+    // operators per (frequency, distinct slowness) pair instead of the table
+    // (kPairs): `slow` holds every point's pair index within its row, `taps`
+    // the operators of rows [pair_z0, ...) in pair order
+    const int* pair_cnt;          // [nz] distinct slowness values of each row
+    const long long* pair_base;   // [nz+1] first pair of each row
+    int pair_z0;
     // per-depth form
     const float2* in;
     float2* out;
@@ -55,7 +61,7 @@ __host__ __device__ inline PersistentSmem persistent_layout(int W, int lines, in
     PersistentSmem s;
     s.mbar = 0;
     s.qs = 8 * (kRowSlots + 4);  // row-staging barriers, then halo barriers [side][parity]
-    s.vbuf = align16(s.qs + 4 * (size_t)lines);
+    s.vbuf = align16(s.qs + 8 * (size_t)lines);  // per-line lookup factors [2][lines]
     s.sbuf = s.vbuf + kRowSlots * (size_t)W * 4;
     s.img = align16(s.sbuf + 2 * (size_t)W * 4);
     s.wave = align16(s.img + (img ? 2 * (size_t)lines * W * 4 : 0));
@@ -99,12 +105,21 @@ __device__ __forceinline__ void put_output(const SegCtx& g, typename WS::T* nxt,
     if (push) push_halo<LT, WS>(g, nxt_off, s, x, v, pb);
 }
 
+// Operator index of a point with staged row value v: the table entry of
+// Sec. III for line factor q (table form), or, with kPairs, the pair index
+// line offset + v (v holds the point's distinct-value index).
+template <bool kPairs>
+__device__ __forceinline__ int op_index(float q, float v, int nk) {
+    if constexpr (kPairs) return __float_as_int(q) + __float_as_int(v);
+    else return table_index(q, v, nk);
+}
+
 // One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
 // extrapolated with the operator of the first output.  Returns the mask of
 // outputs whose own operator differs (the velocity changes inside the 8):
 // those are left unwritten for fir1.  With an imaging buffer (imgz), the real
 // parts of the current wavefield go there.
-template <int LT, class WS, class TP>
+template <int LT, class WS, class TP, bool kPairs>
 __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, bool edge, bool push, int pb,
                                               const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
                                               const float* srow, const float* qs, float* imgz,
@@ -112,7 +127,7 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, b
     float s8[8];
     load_s8(srow + xl0, s8);
     const float q = qs[s];
-    const int idx0 = table_index(q, s8[0], g.nk);
+    const int idx0 = op_index<kPairs>(q, s8[0], g.nk);
     uint32_t skip = 0;
     bool same = true;
 #pragma unroll
@@ -121,7 +136,7 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, b
         const int nvalid = min(8, g.wv - xl0);
 #pragma unroll
         for (int r = 1; r < 8; ++r)
-            if (r < nvalid && table_index(q, s8[r], g.nk) != idx0) skip |= 1u << r;
+            if (r < nvalid && op_index<kPairs>(q, s8[r], g.nk) != idx0) skip |= 1u << r;
     }
     u64 res[8];
     float re[8];
@@ -153,7 +168,7 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, b
 // Warp-cooperative recomputation of the outputs flagged in each lane's
 // `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
 // numbered and taken one per lane.  All 32 lanes must call.
-template <int LT, class WS, class TP>
+template <int LT, class WS, class TP, bool kPairs>
 __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0,
                                             const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
                                             const float* srow, const float* qs,
@@ -184,7 +199,7 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
         if (it < total) {
             const int r = (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
             const int x = x0_o + r;
-            const int idx = table_index(qs[s_o], srow[x], g.nk);
+            const int idx = op_index<kPairs>(qs[s_o], srow[x], g.nk);
             put_output<LT, WS>(g, nxt, nxt_off, s_o, x,
                                fir1<LT, WS, TP>(cur + (size_t)s_o * g.SP, x, taps + (size_t)idx * (LT + 1)), push,
                                pb);
@@ -201,10 +216,10 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 // dynamic shared memory (persistent_layout).  On return every mbarrier used
 // is invalidated and no copy or remote store is in flight, so the memory can
 // hold the next group.
-template <int LT, class WS, class TP>
+template <int LT, class WS, class TP, bool kPairs = false>
 __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
-    const typename TP::E* __restrict__ taps = static_cast<const typename TP::E*>(a.taps);
+    const typename TP::E* __restrict__ taps_all = static_cast<const typename TP::E*>(a.taps);
     const int W = a.W, m = a.lines, C = a.C;
     const int SP = seg_phys_len(W, LT);
     const int NC = W >> 3;
@@ -226,7 +241,18 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
 
     // ---- prologue: zero both wavefield buffers (halos outside [0, nx) stay 0)
     for (int i = tid; i < 2 * m * SP; i += nthr) wave[i] = WS::zero();
-    for (int s = tid; s < m; s += nthr) qs[s] = (s < mg) ? q_of_line(a.i0, l_begin + s, a.nt, a.dt, a.dk) : 0.f;
+    // per-line lookup factors: the table factor q_w (constant), or with
+    // kPairs the line's pair offset in the row, (line) x (distinct values of
+    // the row), refreshed one step ahead in qs[(z & 1) * m + s]
+    auto pair_offsets = [&](int z, float* dst) {
+        const int cnt = a.pair_cnt[z];
+        for (int s = tid; s < m; s += nthr) dst[s] = __int_as_float((s < mg) ? (l_begin + s) * cnt : 0);
+    };
+    if constexpr (kPairs) {
+        pair_offsets(a.z_begin, qs + (a.z_begin & 1) * m);
+    } else {
+        for (int s = tid; s < m; s += nthr) qs[s] = (s < mg) ? q_of_line(a.i0, l_begin + s, a.nt, a.dt, a.dk) : 0.f;
+    }
     uint64_t* hbar = mbar + kRowSlots;  // [side 0 left, 1 right][parity]
     if (tid == 0) {
         for (int b = 0; b < kRowSlots + 4; ++b) mbar_init(&mbar[b], 1);
@@ -371,6 +397,9 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         const int zb = (z - a.z_begin) & 1;
         const T* cur = wave + (size_t)zb * m * SP;
         T* nxt = wave + (size_t)(zb ^ 1) * m * SP;
+        const float* qz = kPairs ? qs + (z & 1) * m : qs;
+        const typename TP::E* __restrict__ taps =
+            kPairs ? taps_all + (size_t)(a.pair_base[z] - a.pair_base[a.pair_z0]) * (LT + 1) : taps_all;
         float* imgz = img ? img + (size_t)(z & 1) * m * W : nullptr;
         const size_t nxt_off = (size_t)(zb ^ 1) * m * SP;
         const float* srow = srow_of(z);
@@ -423,17 +452,21 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             }
             uint32_t mask = 0;
             if (work) {
-                mask = main_item<LT, WS, TP>(sc, s, xl0, edge, push, pb, cur, nxt, nxt_off, srow, qs, imgz, taps);
+                mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, edge, push, pb, cur, nxt, nxt_off, srow, qz, imgz,
+                                                     taps);
             } else if (edge && push && item < n_items) {
                 // beyond the line end: the neighbours still expect zeros
 #pragma unroll
                 for (int r = 0; r < 8; ++r) push_halo<LT, WS>(sc, nxt_off, s, xl0 + r, 0ull, pb);
             }
             if (__any_sync(0xffffffffu, mask != 0u))
-                coop_fixups<LT, WS, TP>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qs, taps, lane, push, pb);
+                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qz, taps, lane, push, pb);
         }
         // velocity rows are converted by the whole CTA one step ahead
         if (!a.slow && z + 1 < a.z_end) convert_row(z + 1);
+        if constexpr (kPairs) {
+            if (z + 1 < a.z_end) pair_offsets(z + 1, qs + ((z + 1) & 1) * m);
+        }
         {
             const int zw = a.slow ? z + 1 : z + 2;
             if (tid == 0 && zw < a.z_end) wait_row(zw);
@@ -457,17 +490,17 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
 
 // One launch of the persistent form: cluster blockIdx.x / C runs group
 // blockIdx.x / C of the problem.
-template <int LT, class WS, class TP>
+template <int LT, class WS, class TP, bool kPairs = false>
 __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_group<LT, WS, TP>(a, (int)(blockIdx.x / a.C), smem);
+    run_group<LT, WS, TP, kPairs>(a, (int)(blockIdx.x / a.C), smem);
 }
 
 
 // One launch of the persistent form for compiled LT and storage policies.
-template <int LT, class WS, class TP>
+template <int LT, class WS, class TP, bool kPairs = false>
 cudaError_t launch_persistent(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
-    auto kern = k_migrate_persistent<LT, WS, TP>;
+    auto kern = k_migrate_persistent<LT, WS, TP, kPairs>;
     cudaError_t e = ensure_smem(kern, plan.smem, plan.cluster > 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

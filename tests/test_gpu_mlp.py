@@ -201,7 +201,7 @@ def _desc_of(fx, wl, k_max):
                    dt=wl.dt, theta_max_deg=wl.theta_deg, k_max=k_max)
 
 
-@pytest.mark.parametrize("nx,nz,lens", [(200, 24, True), (300, 16, False)])
+@pytest.mark.parametrize("nx,nz,lens", [(200, 24, True), (300, 16, False), (203, 16, True)])
 def test_mlp_migrate_matches_pointwise_oracle(fx, oracle_mod, nx, nz, lens):
     wl, vm, w, P0 = _layered(nx, nz, seed=21, lens=lens)
     k_max = float(w.max() / vm.min())
