@@ -129,15 +129,39 @@ struct WeightSmem {
     float W1[kH], b1[kH], b2[kH], b3[kH], b4[kMlpMaxOut];
 };
 
+// Four consecutive weights of row-major W[out][64] as split BF16 pairs.
+__device__ __forceinline__ void split4(float4 v, bf16* hi, bf16* lo) {
+    split(v.x, hi[0], lo[0]);
+    split(v.y, hi[1], lo[1]);
+    split(v.z, hi[2], lo[2]);
+    split(v.w, hi[3], lo[3]);
+}
+
+// Parameters are read as float4 when the array is 16-byte aligned (the
+// matrix offsets are multiples of 4 floats), else one by one.
 __device__ void load_weights(WeightSmem& S, const float* __restrict__ p, int no) {
-    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-        const int r = i / kH, c = i - r * kH;
-        split(p[oW2() + i], S.W2h[r * kLd + c], S.W2l[r * kLd + c]);
-        split(p[oW3() + i], S.W3h[r * kLd + c], S.W3l[r * kLd + c]);
-    }
-    for (int i = threadIdx.x; i < kMlpMaxOut * kH; i += blockDim.x) {
-        const int r = i / kH, c = i - r * kH;
-        split(r < no ? p[oW4() + i] : 0.f, S.W4h[r * kLd + c], S.W4l[r * kLd + c]);
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        for (int i = threadIdx.x; i < kH * kH / 4; i += blockDim.x) {
+            const int r = (4 * i) / kH, c = 4 * i - r * kH;
+            split4(__ldg(p4 + oW2() / 4 + i), S.W2h + r * kLd + c, S.W2l + r * kLd + c);
+            split4(__ldg(p4 + oW3() / 4 + i), S.W3h + r * kLd + c, S.W3l + r * kLd + c);
+        }
+        for (int i = threadIdx.x; i < kMlpMaxOut * kH / 4; i += blockDim.x) {
+            const int r = (4 * i) / kH, c = 4 * i - r * kH;
+            const float4 v = r < no ? __ldg(p4 + oW4() / 4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            split4(v, S.W4h + r * kLd + c, S.W4l + r * kLd + c);
+        }
+    } else {
+        for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+            const int r = i / kH, c = i - r * kH;
+            split(p[oW2() + i], S.W2h[r * kLd + c], S.W2l[r * kLd + c]);
+            split(p[oW3() + i], S.W3h[r * kLd + c], S.W3l[r * kLd + c]);
+        }
+        for (int i = threadIdx.x; i < kMlpMaxOut * kH; i += blockDim.x) {
+            const int r = i / kH, c = i - r * kH;
+            split(r < no ? p[oW4() + i] : 0.f, S.W4h[r * kLd + c], S.W4l[r * kLd + c]);
+        }
     }
     for (int i = threadIdx.x; i < kH; i += blockDim.x) {
         S.W1[i] = p[oW1() + i];
@@ -424,25 +448,37 @@ struct InferArgs {
     float4* taps_k;           // pair p of the block at taps_k[(p - base[z0]) * (LT + 1)]
 };
 
+// Row-block inputs staged in shared memory after the weights: the block's
+// pair offsets base[z0..z1] (relative to base[z0]), distinct-value counts,
+// and the frequency factors q_w = fl32(w / k_max).
+constexpr int kMaxBlockRows = 64;
+struct BlockTables {
+    long long base[kMaxBlockRows + 1];
+    int cnt[kMaxBlockRows];
+    float q[1];  // [nw]
+};
+__host__ __device__ inline size_t block_tables_bytes(int nw) {
+    return sizeof(BlockTables) + (size_t)(nw > 0 ? nw - 1 : 0) * sizeof(float);
+}
+
 __device__ __forceinline__ float q_of_line_mlp(int i0, int j, int nt, double dt, double inv_kmax) {
     const double w = 2.0 * 3.14159265358979323846 * (double)(i0 + j) / ((double)nt * dt);
     return __double2float_rn(w * inv_kmax);
 }
 
-// Input of pair p in the row block (binary search of the row, then
-// frequency / distinct value within the row).
-__device__ __forceinline__ float block_input(const InferArgs& a, long long p) {
-    int lo = a.z0, hi = a.z1 - 1;
+// Input of pair p (relative to the block's first pair) in the row block:
+// binary search of the row, then frequency / distinct value within the row,
+// from the staged tables.
+__device__ __forceinline__ float block_input(const InferArgs& a, const BlockTables& T, long long p) {
+    int lo = 0, hi = a.z1 - a.z0 - 1;
     while (lo < hi) {  // last row with base[row] <= p
         const int mid = (lo + hi + 1) >> 1;
-        if (a.base[mid] <= p) lo = mid; else hi = mid - 1;
+        if (T.base[mid] <= p) lo = mid; else hi = mid - 1;
     }
-    const int z = lo;
-    const long long j = p - a.base[z];
-    const int c = a.cnt[z];
-    const int w = (int)(j / c), u = (int)(j - (long long)w * c);
-    const float q = q_of_line_mlp(a.i0, w, a.nt, a.dt, a.inv_kmax);
-    const float x = __fmul_rn(q, a.uval[(size_t)z * a.nx + u]);
+    const int j = (int)(p - T.base[lo]);  // < nw * nx < 2^31
+    const int c = T.cnt[lo];
+    const int w = j / c, u = j - w * c;
+    const float x = __fmul_rn(T.q[w], a.uval[(size_t)(a.z0 + lo) * a.nx + u]);
     return fminf(fmaxf(x, 0.f), 1.f);  // the network is defined on [0, 1]; NaN maps to 0
 }
 
@@ -498,15 +534,21 @@ __device__ __forceinline__ void infer_hidden(const bf16* Wh, const bf16* Wl, con
 __global__ void __launch_bounds__(kInferWarps * 32) k_mlp_infer(const InferArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     WeightSmem& S = *reinterpret_cast<WeightSmem*>(smraw);
+    BlockTables& T = *reinterpret_cast<BlockTables*>(smraw + sizeof(WeightSmem));
     load_weights(S, a.params, a.no);
+    long long total = a.n;
+    if (!a.kv) {
+        const long long first = a.base[a.z0];
+        for (int i = threadIdx.x; i <= a.z1 - a.z0; i += blockDim.x) {
+            T.base[i] = a.base[a.z0 + i] - first;
+            if (i < a.z1 - a.z0) T.cnt[i] = a.cnt[a.z0 + i];
+        }
+        for (int j = threadIdx.x; j < a.nw; j += blockDim.x) T.q[j] = q_of_line_mlp(a.i0, j, a.nt, a.dt, a.inv_kmax);
+        total = a.base[a.z1] - first;
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    long long first = 0, total = a.n;
-    if (!a.kv) {
-        first = a.base[a.z0];
-        total = a.base[a.z1] - first;
-    }
     const long long tiles = (total + 15) / 16;
     for (long long tile = (long long)blockIdx.x * kInferWarps + warp; tile < tiles;
          tile += (long long)gridDim.x * kInferWarps) {
@@ -517,8 +559,8 @@ __global__ void __launch_bounds__(kInferWarps * 32) k_mlp_infer(const InferArgs 
             if (r_g < total) xg = fminf(fmaxf((float)(a.kv[r_g] * a.inv_kmax), 0.f), 1.f);
             if (r_g8 < total) xg8 = fminf(fmaxf((float)(a.kv[r_g8] * a.inv_kmax), 0.f), 1.f);
         } else {
-            if (r_g < total) xg = block_input(a, first + r_g);
-            if (r_g8 < total) xg8 = block_input(a, first + r_g8);
+            if (r_g < total) xg = block_input(a, T, r_g);
+            if (r_g8 < total) xg8 = block_input(a, T, r_g8);
         }
         uint32_t ah[4][4], al[4][4];
         infer_layer1(S, xg, xg8, t, ah, al);
@@ -566,7 +608,7 @@ static int sm_count() {
 }
 
 static cudaError_t launch_infer(const InferArgs& a, long long max_total, cudaStream_t s) {
-    const size_t smem = sizeof(WeightSmem);
+    const size_t smem = sizeof(WeightSmem) + (a.kv ? 0 : block_tables_bytes(a.nw));
     cudaError_t e = ensure_smem(k_mlp_infer, smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (max_total + 15) / 16;
@@ -613,6 +655,7 @@ cudaError_t launch_mlp_block_taps(const fxmig_desc* d, int LT, const float* para
     a.nt = d->nt;
     a.dt = d->dt;
     a.taps_k = taps;
+    if (z1 - z0 > kMaxBlockRows) return cudaErrorInvalidValue;
     // grid sized for the worst case: every sample of every row distinct
     return launch_infer(a, (long long)(z1 - z0) * d->nx * d->nw, s);
 }
