@@ -371,6 +371,16 @@ int fxmig_batch_autotune(const fxmig_line *lines, int n, fxmig_batch_plan *plan,
 int fxmig_migrate_batch(const fxmig_line *lines, int n, const fxmig_batch_plan *plan, void *ws,
                         size_t ws_bytes, void *stream);
 
+/* Self-test of device-side failure reporting (the paper has no
+ * counterpart).  Runs the bounded mbarrier wait that the depth loops use
+ * against a barrier that nothing arrives at; after `polls` polls
+ * (1 <= polls <= 2^20) the wait gives up, the kernel records the timeout in the
+ * status word of `ws` (cleared first) and returns normally.  fxmig_check(ws)
+ * then returns FXMIG_ETIMEOUT, and the CUDA context stays usable.
+ *   ws  device, at least 256 bytes, 256-byte aligned (any workspace works)
+ * Errors: FXMIG_EINVAL, FXMIG_ECUDA. */
+int fxmig_selftest_timeout(void *ws, int polls, void *stream);
+
 /* Waits for `stream`, then reads and returns the device status word in `ws`
  * (FXMIG_OK, FXMIG_EVELOCITY or FXMIG_ETIMEOUT); FXMIG_ECUDA if the stream
  * reports a CUDA error; FXMIG_EINVAL for a NULL ws. */

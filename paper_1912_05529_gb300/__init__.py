@@ -26,7 +26,7 @@ __all__ = [
     "FxmigError", "Desc", "Launch", "lib", "library_path",
     "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
     "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
-    "fxmig_check", "fxmig_migrate_noalloc", "desc_for", "migrate_section",
+    "fxmig_check", "fxmig_migrate_noalloc", "fxmig_selftest_timeout", "desc_for", "migrate_section",
     "fxmig_mlp_param_count", "fxmig_mlp_train_ws_bytes", "fxmig_design_at", "fxmig_mlp_train",
     "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials", "fxmig_mlp_migrate",
     "Line", "BatchPlan", "line_of", "fxmig_batch_workspace_bytes", "fxmig_batch_num_partials",
@@ -104,6 +104,7 @@ def lib():
         L.fxmig_migrate_ex.argtypes = [pd, pl, vp, vp, vp, vp, i, i, i, vp, sz, vp]
         L.fxmig_image.argtypes = [pd, vp, i, vp, vp]
         L.fxmig_check.argtypes = [vp, vp]
+        L.fxmig_selftest_timeout.argtypes = [vp, i, vp]
         fl = ctypes.c_float
         L.fxmig_mlp_param_count.argtypes = [i]
         L.fxmig_mlp_train_ws_bytes.argtypes = [i, i]
@@ -124,7 +125,7 @@ def lib():
                   "fxmig_image", "fxmig_check", "fxmig_mlp_param_count", "fxmig_design_at",
                   "fxmig_mlp_train", "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials",
                   "fxmig_mlp_migrate", "fxmig_batch_num_partials", "fxmig_batch_autotune",
-                  "fxmig_migrate_batch"):
+                  "fxmig_migrate_batch", "fxmig_selftest_timeout"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -242,6 +243,12 @@ def fxmig_image(d: Desc, partials, image, stream=None) -> None:
 def fxmig_check(ws, stream=None) -> int:
     """Synchronise the stream and return the device status code (0 = ok)."""
     return int(lib().fxmig_check(_dev_ptr(ws, "ws"), _stream(stream)))
+
+
+def fxmig_selftest_timeout(ws, polls: int = 1000, stream=None) -> None:
+    """Make the device's bounded wait give up once (nothing arrives at its
+    barrier); fxmig_check(ws) then reports FXMIG_ETIMEOUT."""
+    _check(lib().fxmig_selftest_timeout(_dev_ptr(ws, "ws"), int(polls), _stream(stream)), "fxmig_selftest_timeout")
 
 
 def fxmig_migrate_noalloc(d: Desc, slab, vel, table, partials, z_begin, z_end, stream=None) -> None:

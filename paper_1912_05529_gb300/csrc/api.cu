@@ -266,6 +266,12 @@ int fxmig_migrate_batch(const fxmig_line* lines, int n, const fxmig_batch_plan* 
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate_batch");
 }
 
+int fxmig_selftest_timeout(void* ws, int polls, void* stream) {
+    if (!ws || !aligned(ws, 256) || polls < 1 || polls > (1 << 20)) return FXMIG_EINVAL;
+    const cudaError_t e = launch_selftest_timeout(ws, polls, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_selftest_timeout");
+}
+
 int fxmig_check(const void* ws, void* stream) {
     if (!ws) return FXMIG_EINVAL;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);

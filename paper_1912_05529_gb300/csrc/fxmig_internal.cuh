@@ -218,6 +218,7 @@ int batch_num_partials(const fxmig_line* lines, int n, const fxmig_batch_plan* p
 cudaError_t launch_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, void* ws, cudaStream_t s);
 int batch_autotune(const fxmig_line* lines, int n, fxmig_batch_plan* out, void* ws, cudaStream_t s,
                    float* best_ms);
+cudaError_t launch_selftest_timeout(void* ws, int polls, cudaStream_t s);
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
                          cudaStream_t s);
 

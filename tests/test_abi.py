@@ -192,3 +192,12 @@ def test_batch_entry_points_reject_bad_arguments(fx):
     assert lib.fxmig_migrate_batch(arr2, 1, None, ok, need, None) == fx.FXMIG_EINVAL
     plan = fx.BatchPlan()
     assert lib.fxmig_batch_autotune(arr, 2, ctypes.byref(plan), None, ok, need, None) == fx.FXMIG_ENOSPC
+
+
+def test_selftest_rejects_bad_arguments(fx):
+    lib = fx.lib()
+    ok = ctypes.c_void_p(1 << 20)
+    assert lib.fxmig_selftest_timeout(None, 100, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_selftest_timeout(ctypes.c_void_p((1 << 20) + 8), 100, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_selftest_timeout(ok, 0, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig_selftest_timeout(ok, (1 << 20) + 1, None) == fx.FXMIG_EINVAL
