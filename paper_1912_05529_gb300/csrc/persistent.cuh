@@ -388,9 +388,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
     const int n_items = mg * NC;
     // item / NC by a multiply-high with m = ceil(2^32 / NC): exact while
-    // item * NC < 2^32, which n_items * NC < 2^32 guarantees
+    // item * NC < 2^32, which n_items * NC < 2^32 guarantees; m fits 32 bits
+    // only for NC >= 2 (NC = 1 divides exactly)
     const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
-    const bool magic_ok = (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
+    const bool magic_ok = NC >= 2 && (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
     const bool spread = (NC & 31) == 0;  // lines of whole warps of items
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
