@@ -49,3 +49,20 @@ def test_band_to_time_inverts_band_dft(oracle_mod):
     P = rng.standard_normal((nw, 5)) + 1j * rng.standard_normal((nw, 5))
     d = oracle_mod.band_to_time(P, i0, nt)
     assert np.linalg.norm(oracle_mod.band_dft(d, i0, nw) - P) / np.linalg.norm(P) < 1e-12
+
+
+def test_ricker_spectrum_matches_dft_of_samples(oracle_mod):
+    # zero-phase Ricker samples: their DFT is dt-spaced samples of the
+    # continuous spectrum divided by dt (aliasing is negligible at 1 ms)
+    import workloads as W
+    dt, nt, fp = 0.001, 4096, 25.0
+    t = (np.arange(nt) - nt // 2) * dt
+    r = W.ricker(t, fp)
+    dft = np.fft.rfft(np.fft.ifftshift(r))
+    f = np.fft.rfftfreq(nt, dt)
+    S = oracle_mod.ricker_spectrum(f, fp, dt)
+    assert np.max(np.abs(dft.imag)) <= 1e-9 * np.max(np.abs(dft))
+    assert np.max(np.abs(dft.real - S)) <= 1e-9 * np.max(S)
+    # the amplitude spectrum peaks at the peak frequency
+    fine = np.linspace(1.0, 100.0, 99001)
+    assert abs(fine[np.argmax(oracle_mod.ricker_spectrum(fine, fp))] - fp) < 1e-3
