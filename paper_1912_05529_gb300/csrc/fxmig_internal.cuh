@@ -143,6 +143,14 @@ __device__ __forceinline__ void st_async_v2(uint32_t addr, float2 v, uint32_t re
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
                  :: "r"(addr), "f"(v.x), "f"(v.y), "r"(remote_bar) : "memory");
 }
+// Bulk copy of `bytes` from this CTA's shared memory into another CTA's of
+// the cluster (dst and remote_bar are shared::cluster addresses), counted on
+// that CTA's mbarrier; 16-byte aligned addresses, bytes a multiple of 16.
+// The copy engine moves the data: the issuing thread does not wait.
+__device__ __forceinline__ void bulk_s2cluster(uint32_t dst, const void* src, uint32_t bytes, uint32_t remote_bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "r"(smem_u32(src)), "r"(bytes), "r"(remote_bar) : "memory");
+}
 // Bounded wait with cluster-scope acquire (data written by other CTAs).
 __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
     const uint32_t a = smem_u32(bar);

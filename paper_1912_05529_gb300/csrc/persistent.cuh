@@ -94,17 +94,6 @@ __device__ __forceinline__ void push_halo(const SegCtx& g, size_t nxt_off, int s
                      pb ? g.bar_right[1] : g.bar_right[0]);
 }
 
-// Write one output (local position x of line s) to the next buffer and, when
-// `push` is set and it lies within LT of a segment edge, into the halo of the
-// neighbour on that side (st.async, counted on the neighbour's halo barrier
-// of parity pb).
-template <int LT, class WS>
-__device__ __forceinline__ void put_output(const SegCtx& g, typename WS::T* nxt, size_t nxt_off, int s, int x,
-                                           u64 v, bool push, int pb) {
-    WS::st1(nxt + (size_t)s * g.SP + phys(x + LT), v);
-    if (push) push_halo<LT, WS>(g, nxt_off, s, x, v, pb);
-}
-
 // Operator index of a point with staged row value v: the table entry of
 // Sec. III for line factor q (table form), or, with kPairs, the pair index
 // line offset + v (v holds the point's distinct-value index).
@@ -114,15 +103,28 @@ __device__ __forceinline__ int op_index(float q, float v, int nk) {
     else return table_index(q, v, nk);
 }
 
+// Bring the operator row tp[0..LT] into L1 ahead of its use (the rows of
+// operator changes are read by the fixup round after the main item).
+template <int LT, class TP>
+__device__ __forceinline__ void prefetch_taps(const typename TP::E* tp) {
+    constexpr int kBytes = (LT + 1) * (int)sizeof(typename TP::E);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(tp);
+#pragma unroll
+    for (int o = 0; o < kBytes + 127; o += 128) {
+        const uintptr_t a = (a0 & ~uintptr_t(127)) + (uintptr_t)o;
+        if (a < a0 + kBytes) asm volatile("prefetch.global.L1 [%0];" :: "l"(a));
+    }
+}
+
 // One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
 // extrapolated with the operator of the first output.  Returns the mask of
 // outputs whose own operator differs (the velocity changes inside the 8):
-// those are left unwritten for fir1.  With an imaging buffer (imgz), the real
+// those are left unwritten for the fixup round, and their operator rows are
+// prefetched into L1 meanwhile.  With an imaging buffer (imgz), the real
 // parts of the current wavefield go there.
 template <int LT, class WS, class TP, bool kPairs>
-__device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, bool edge, bool push, int pb,
-                                              const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
-                                              const float* srow, const float* qs, float* imgz,
+__device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, const typename WS::T* cur,
+                                              typename WS::T* nxt, const float* srow, const float* qs, float* imgz,
                                               const typename TP::E* __restrict__ taps) {
     float s8[8];
     load_s8(srow + xl0, s8);
@@ -134,9 +136,16 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, b
     for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
     if (!same) {
         const int nvalid = min(8, g.wv - xl0);
+        int last = idx0;
 #pragma unroll
-        for (int r = 1; r < 8; ++r)
-            if (r < nvalid && op_index<kPairs>(q, s8[r], g.nk) != idx0) skip |= 1u << r;
+        for (int r = 1; r < 8; ++r) {
+            const int idx = op_index<kPairs>(q, s8[r], g.nk);
+            if (r < nvalid && idx != idx0) {
+                skip |= 1u << r;
+                if (idx != last) prefetch_taps<LT, TP>(taps + (size_t)idx * (LT + 1));
+                last = idx;
+            }
+        }
     }
     u64 res[8];
     float re[8];
@@ -151,28 +160,20 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, b
         for (int r = 0; r < 8; ++r)
             if (xl0 + r >= g.wv) res[r] = 0ull;
     }
+    typename WS::T* dst = nxt + (size_t)s * g.SP;
     if (skip == 0) {
-        store8<LT, WS>(nxt + (size_t)s * g.SP + (xl0 >> 3) * 10, res);
-        if (edge && push) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) push_halo<LT, WS>(g, nxt_off, s, xl0 + r, res[r], pb);
-        }
+        store8<LT, WS>(dst + (xl0 >> 3) * 10, res);
     } else {
 #pragma unroll
         for (int r = 0; r < 8; ++r)
-            if (!((skip >> r) & 1u)) put_output<LT, WS>(g, nxt, nxt_off, s, xl0 + r, res[r], edge && push, pb);
+            if (!((skip >> r) & 1u)) WS::st1(dst + phys(xl0 + r + LT), res[r]);
     }
     return skip;
 }
 
-// Warp-cooperative recomputation of the outputs flagged in each lane's
-// `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
-// numbered and taken one per lane.  All 32 lanes must call.
-template <int LT, class WS, class TP, bool kPairs>
-__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0,
-                                            const typename WS::T* cur, typename WS::T* nxt, size_t nxt_off,
-                                            const float* srow, const float* qs,
-                                            const typename TP::E* __restrict__ taps, int lane, bool push, int pb) {
+// Number the set bits of each lane's mask across the warp: returns the
+// warp total; excl receives the bits of the lanes below.
+__device__ __forceinline__ uint32_t warp_enumerate(uint32_t mask, int lane, uint32_t& excl) {
     const uint32_t cnt = __popc(mask);
     uint32_t incl = cnt;
 #pragma unroll
@@ -180,18 +181,35 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
         const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
-    const uint32_t excl = incl - cnt;
+    excl = incl - cnt;
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// The lane that owns bit number it of the warp's enumeration (excl from
+// warp_enumerate), found by a binary search over the lanes' prefix counts.
+__device__ __forceinline__ int warp_owner(uint32_t excl, uint32_t it) {
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int cand = owner + step;
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, cand);
+        if (ex <= it) owner = cand;
+    }
+    return owner;
+}
+
+// Warp-cooperative recomputation of the outputs flagged in each lane's
+// `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
+// numbered and taken one per lane.  All 32 lanes must call.
+template <int LT, class WS, class TP, bool kPairs>
+__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0,
+                                            const typename WS::T* cur, typename WS::T* nxt, const float* srow,
+                                            const float* qs, const typename TP::E* __restrict__ taps, int lane) {
+    uint32_t excl;
+    const uint32_t total = warp_enumerate(mask, lane, excl);
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t it = base + lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = owner + step;
-            const uint32_t ex = __shfl_sync(0xffffffffu, excl, cand);
-            if (ex <= it) owner = cand;
-        }
+        const int owner = warp_owner(excl, it);
         const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
         const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
         const int s_o = __shfl_sync(0xffffffffu, s, owner);
@@ -200,11 +218,65 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
             const int r = (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
             const int x = x0_o + r;
             const int idx = op_index<kPairs>(qs[s_o], srow[x], g.nk);
-            put_output<LT, WS>(g, nxt, nxt_off, s_o, x,
-                               fir1<LT, WS, TP>(cur + (size_t)s_o * g.SP, x, taps + (size_t)idx * (LT + 1)), push,
-                               pb);
+            WS::st1(nxt + (size_t)s_o * g.SP + phys(x + LT),
+                    fir1<LT, WS, TP>(cur + (size_t)s_o * g.SP, x, taps + (size_t)idx * (LT + 1)));
         }
     }
+}
+
+// Warp-cooperative halo push of the round's edge outputs: bit r of a lane's
+// `mask` marks output xl0 + r of line s, which lies within LT of a segment
+// edge that has a neighbour.  The outputs are numbered across the warp and
+// sent one per lane from the next buffer (written by this warp's main items
+// and fixups before the __syncwarp that precedes the call), so the remote
+// stores of a round go out as a few warp-wide st.async.  All 32 lanes must
+// call.
+template <int LT, class WS>
+__device__ __forceinline__ void coop_push(const SegCtx& g, uint32_t mask, int s, int xl0,
+                                          const typename WS::T* nxt, size_t nxt_off, int lane, int pb) {
+    uint32_t excl;
+    const uint32_t total = warp_enumerate(mask, lane, excl);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t it = base + lane;
+        const int owner = warp_owner(excl, it);
+        const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
+        const int s_o = __shfl_sync(0xffffffffu, s, owner);
+        const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
+        if (it < total) {
+            const int x = x0_o + (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
+            push_halo<LT, WS>(g, nxt_off, s_o, x, WS::ld1(nxt + (size_t)s_o * g.SP + phys(x + LT)), pb);
+        }
+    }
+}
+
+// Halo strips of one line in the padded layout, pads included.  The left
+// strip holds outputs x in [0, LT) at slots [phys(LT), phys(2LT-1)] and
+// lands phys(W) slots further on in the left neighbour's right halo; the
+// right strip holds x in [W-LT, W) at slots phys(W) + [0, phys(LT-1)] and
+// lands at slot 0 of the right neighbour's line (W a multiple of 8, so the
+// pad pattern is the same on both sides).
+template <int LT>
+struct HaloStrips {
+    static constexpr int kLeft0 = LT + 2 * (LT >> 3);
+    static constexpr int kLeftN = (2 * LT - 1) + 2 * ((2 * LT - 1) >> 3) + 1 - kLeft0;
+    static constexpr int kRightN = (LT - 1) + 2 * ((LT - 1) >> 3) + 1;
+};
+
+// Send slots [0, n) of a strip from this CTA's shared memory (src) to the
+// neighbour's (dst, shared::cluster), counted on the neighbour's mbarrier.
+// src and dst have the same address modulo 16 bytes: the 16-byte aligned
+// middle goes as one bulk copy (the copy engine moves it; the thread does not
+// wait), the slots before and after it by st.async.  The caller has fenced
+// the strip's shared-memory writes for the async proxy.
+template <class WS>
+__device__ __forceinline__ void send_strip(uint32_t dst, const typename WS::T* src, int n, uint32_t bar) {
+    constexpr int kB = WS::kBytes;
+    const int head = min(n, (int)(((16u - (smem_u32(src) & 15u)) & 15u) / kB));
+    const int body = ((n - head) * kB / 16) * 16 / kB;
+    for (int i = 0; i < head; ++i) WS::st_async(dst + (uint32_t)(i * kB), WS::ld1(src + i), bar);
+    if (body > 0) bulk_s2cluster(dst + (uint32_t)(head * kB), src + head, (uint32_t)(body * kB), bar);
+    for (int i = head + body; i < n; ++i) WS::st_async(dst + (uint32_t)(i * kB), WS::ld1(src + i), bar);
 }
 
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
@@ -313,15 +385,15 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         if (bad) atomicOr(a.status, kStatusVelocity);
     };
     // partial[g][z][x0 + x] = sum over the group's lines (ascending) of Re P at
-    // depth z: from the imaging buffer after the step barrier, or (no buffer)
-    // from the step's input wavefield, which nobody writes during the step,
-    // before the barrier
+    // depth z, by threads t = 0..nt-1: from the imaging buffer after the step
+    // barrier, or (no buffer) from the step's input wavefield, which nobody
+    // writes during the step, before the barrier
     const int part = a.part_fixed ? a.part : g;
-    auto reduce_image_row = [&](int z, const T* cur) {
+    auto reduce_image_row = [&](int z, const T* cur, int t, int nt) {
         float* dst = a.partials + ((size_t)part * a.nz + z) * a.nx + x0;
         if (img) {
             const float* src = img + (size_t)(z & 1) * m * W;
-            for (int x = tid * 4; x < wv; x += nthr * 4) {
+            for (int x = t * 4; x < wv; x += nt * 4) {
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int s = 0; s < mg; ++s) {
                     const float4 v = *reinterpret_cast<const float4*>(src + (size_t)s * W + x);
@@ -341,7 +413,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 }
             }
         } else {
-            for (int x = tid; x < wv; x += nthr) {
+            for (int x = t; x < wv; x += nt) {
                 float acc = 0.f;
                 for (int s = 0; s < mg; ++s) acc += WS::to_f2(cur[(size_t)s * SP + phys(x + LT)]).x;
                 dst[x] = a.accumulate ? dst[x] + acc : acc;
@@ -372,19 +444,29 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         sc.bar_left[b] = sc.has_left ? map_cluster_rank(&hbar[2 + b], rank - 1) : 0u;   // its right halo
         sc.bar_right[b] = sc.has_right ? map_cluster_rank(&hbar[b], rank + 1) : 0u;     // its left halo
     }
-    // bytes each halo barrier phase receives: LT outputs of every line
-    const uint32_t halo_bytes = (uint32_t)mg * LT * (uint32_t)WS::kBytes;
+    // Halo pushes: one strip per line and side, sent by the warp that owns
+    // the strip's chunks (the spread mapping below keeps them in one warp)
+    // when a strip and its landing place have the same 16-byte alignment;
+    // else one st.async per output.  Bytes each halo barrier phase receives:
+    // the strips of every line (pads included), or LT outputs of every line.
+    typedef HaloStrips<LT> HS;
+    const int physW = W + 2 * (W >> 3);
+    const bool strips = C > 1 && (W & 7) == 0 && ((W >> 3) & 31) == 0 && (physW * WS::kBytes) % 16 == 0;
+    const uint32_t kB = (uint32_t)WS::kBytes;
+    const uint32_t halo_bytes_l = (uint32_t)mg * (strips ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB);
+    const uint32_t halo_bytes_r = (uint32_t)mg * (strips ? (uint32_t)HS::kLeftN * kB : (uint32_t)LT * kB);
 
     // Work items: (line, 8-output chunk), one per lane and round.  Chunks
-    // within LT of a segment edge ("edge" chunks) read the halo and send their
-    // outputs to the neighbours' halos.  Halo exchange is point to point:
-    // outputs go out with st.async, and a CTA waits on its own halo barrier
-    // of the step's parity before it reads its halo; neighbours can never be
-    // more than one step apart, so two parities suffice and no cluster-wide
+    // within LT of a segment edge ("edge" chunks) read the halo, and their
+    // outputs go to the neighbours' halos.  Halo exchange is point to point:
+    // after each round of items a warp sends its edge outputs with st.async
+    // (one output per lane), and a CTA waits on its own halo barrier of the
+    // step's parity before it reads its halo; neighbours can never be more
+    // than one step apart, so two parities suffice and no cluster-wide
     // barrier is needed.  One CTA barrier ends a depth step; the image row of
     // the step is summed right after it from the imaging buffer (overlapping
-    // the next step's items), or without that buffer just before it from the
-    // step's input wavefield.
+    // the neighbours' halo transfers), or without that buffer just before it
+    // from the step's input wavefield.
     const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
     const int n_items = mg * NC;
     // item / NC by a multiply-high with m = ceil(2^32 / NC): exact while
@@ -393,7 +475,16 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
     const bool magic_ok = NC >= 2 && (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
     const bool spread = (NC & 31) == 0;  // lines of whole warps of items
-
+    // line s and chunk c of a valid item.  With `spread`, a warp's 32 items
+    // of a line, j = 32a + 8q + r, take chunk 8 (q NC/32 + a) + r, so each
+    // warp covers four blocks of 8 chunks a quarter of the line apart
+    // (velocity changes, which cost extra work, are shared between warps); a
+    // quarter-warp keeps 8 consecutive chunks (conflict-free window loads).
+    auto item_chunk = [&](int item, int& s, int& c) {
+        s = magic_ok ? (int)__umulhi((uint32_t)item, nc_magic) : item / NC;
+        const int j = item - s * NC;
+        c = spread ? ((((j >> 3) & 3) * (NC >> 5) + (j >> 5)) << 3) + (j & 7) : j;
+    };
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
         const T* cur = wave + (size_t)zb * m * SP;
@@ -412,28 +503,22 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             // row z+kRowAhead goes to the slot of row z-1, which nobody reads now
             if (z + kRowAhead < a.z_end) issue_row(z + kRowAhead);
             if (halo_wait) {
-                if (sc.has_left) mbar_arrive_expect_tx(&hbar[z & 1], halo_bytes);
-                if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes);
+                if (sc.has_left) mbar_arrive_expect_tx(&hbar[z & 1], halo_bytes_l);
+                if (sc.has_right) mbar_arrive_expect_tx(&hbar[2 + (z & 1)], halo_bytes_r);
             }
         }
 
         for (int base = warp * 32; base < n_items; base += nwarps * 32) {
             const int item = base + lane;
             int s = 0, xl0 = 0;
-            bool work = false, edge = false, need_l = false, need_r = false;
+            bool work = false, need_l = false, need_r = false;
+            uint32_t pmask = 0;  // outputs of the item that go to a neighbour's halo (st.async form)
+            bool issue_l = false, issue_r = false;  // the item's chunk starts / ends its line's strip
             if (item < n_items) {
-                s = magic_ok ? (int)__umulhi((uint32_t)item, nc_magic) : item / NC;
-                const int j = item - s * NC;
-                // spread a warp's 32 items over the line: item j = 32a + 8q + r
-                // takes chunk 8 (q NC/32 + a) + r, so each warp covers four
-                // blocks of 8 chunks a quarter of the line apart (velocity
-                // changes, which cost extra work, are shared between warps);
-                // a quarter-warp keeps 8 consecutive chunks (conflict-free
-                // window loads)
-                const int c = spread ? ((((j >> 3) & 3) * (NC >> 5) + (j >> 5)) << 3) + (j & 7) : j;
+                int c;
+                item_chunk(item, s, c);
                 xl0 = c << 3;
                 work = xl0 < wv;
-                edge = (C > 1) && (c < E || c >= NC - E);
                 // Chunks c < E read the left halo and push to the left
                 // neighbour, chunks c >= NC - E the right ones (both also when
                 // the chunk lies beyond the line end and only pushes zeros).
@@ -442,6 +527,14 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 // pusher waits even when it reads nothing.
                 need_l = sc.has_left && c < E;
                 need_r = sc.has_right && c >= NC - E;
+                if (push && strips) {
+                    issue_l = need_l && c == 0;
+                    issue_r = need_r && c == NC - 1;
+                } else if (push && (need_l || need_r)) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+                        if ((need_l && xl0 + r < LT) || (need_r && xl0 + r >= W - LT)) pmask |= 1u << r;
+                }
             }
             if (halo_wait) {
                 // the neighbours' outputs of step z-1 have landed in cur's halo
@@ -452,16 +545,26 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             uint32_t mask = 0;
-            if (work) {
-                mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, edge, push, pb, cur, nxt, nxt_off, srow, qz, imgz,
-                                                     taps);
-            } else if (edge && push && item < n_items) {
-                // beyond the line end: the neighbours still expect zeros
-#pragma unroll
-                for (int r = 0; r < 8; ++r) push_halo<LT, WS>(sc, nxt_off, s, xl0 + r, 0ull, pb);
-            }
+            if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps);
             if (__any_sync(0xffffffffu, mask != 0u))
-                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, cur, nxt, nxt_off, srow, qz, taps, lane, push, pb);
+                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, cur, nxt, srow, qz, taps, lane);
+            if (__any_sync(0xffffffffu, issue_l || issue_r)) {
+                // the strips' outputs (main items, fixups of this warp) are in
+                // nxt; make them visible to the copy engine, then send
+                fence_proxy_async_smem();
+                __syncwarp();
+                const uint32_t line = (uint32_t)(nxt_off + (size_t)s * SP);
+                if (issue_l)
+                    send_strip<WS>(sc.nb_left + (line + physW + HS::kLeft0) * kB, nxt + (size_t)s * SP + HS::kLeft0,
+                                   HS::kLeftN, pb ? sc.bar_left[1] : sc.bar_left[0]);
+                if (issue_r)
+                    send_strip<WS>(sc.nb_right + line * kB, nxt + (size_t)s * SP + physW, HS::kRightN,
+                                   pb ? sc.bar_right[1] : sc.bar_right[0]);
+            }
+            if (__any_sync(0xffffffffu, pmask != 0u)) {
+                __syncwarp();  // the round's outputs (main items, fixups) are in nxt
+                coop_push<LT, WS>(sc, pmask, s, xl0, nxt, nxt_off, lane, pb);
+            }
         }
         // velocity rows are converted by the whole CTA one step ahead
         if (!a.slow && z + 1 < a.z_end) convert_row(z + 1);
@@ -472,13 +575,16 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             const int zw = a.slow ? z + 1 : z + 2;
             if (tid == 0 && zw < a.z_end) wait_row(zw);
         }
-        if (!img) reduce_image_row(z, cur);
+        if (!img) reduce_image_row(z, cur, tid, nthr);
         __syncthreads();
-        if (img) reduce_image_row(z, cur);  // img[z & 1] is next written at step z + 2
+        // img[z & 1] is next written at step z + 2; the last row is summed
+        // after the final barrier
+        if (img && z + 1 < a.z_end) reduce_image_row(z, cur, tid, nthr);
     }
     // nothing is pushed at the last step and every earlier push has been
     // waited for; the final barrier keeps the CTAs' exits ordered
     if (C > 1) cluster_sync_all(); else __syncthreads();
+    if (img && a.z_end > a.z_begin) reduce_image_row(a.z_end - 1, nullptr, tid, nthr);
     if (tid == 0)
         for (int b = 0; b < kRowSlots + 4; ++b) mbar_inval(&mbar[b]);
 
