@@ -120,32 +120,37 @@ __device__ __forceinline__ void prefetch_taps(const typename TP::E* tp) {
 // extrapolated with the operator of the first output.  Returns the mask of
 // outputs whose own operator differs (the velocity changes inside the 8):
 // those are left unwritten for the fixup round, and their operator rows are
-// prefetched into L1 meanwhile.  With an imaging buffer (imgz), the real
-// parts of the current wavefield go there.
+// prefetched into L1 meanwhile; idx1 receives their operator when they all
+// share one (the usual single change), else -1.  With an imaging buffer
+// (imgz), the real parts of the current wavefield go there.
 template <int LT, class WS, class TP, bool kPairs>
 __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, const typename WS::T* cur,
                                               typename WS::T* nxt, const float* srow, const float* qs, float* imgz,
-                                              const typename TP::E* __restrict__ taps) {
+                                              const typename TP::E* __restrict__ taps, int& idx1) {
     float s8[8];
     load_s8(srow + xl0, s8);
     const float q = qs[s];
     const int idx0 = op_index<kPairs>(q, s8[0], g.nk);
     uint32_t skip = 0;
+    idx1 = -1;
     bool same = true;
 #pragma unroll
     for (int r = 1; r < 8; ++r) same &= (__float_as_uint(s8[r]) == __float_as_uint(s8[0]));
     if (!same) {
         const int nvalid = min(8, g.wv - xl0);
         int last = idx0;
+        bool uni = true;
 #pragma unroll
         for (int r = 1; r < 8; ++r) {
             const int idx = op_index<kPairs>(q, s8[r], g.nk);
             if (r < nvalid && idx != idx0) {
+                uni &= (skip == 0u) || (idx == last);
                 skip |= 1u << r;
                 if (idx != last) prefetch_taps<LT, TP>(taps + (size_t)idx * (LT + 1));
                 last = idx;
             }
         }
+        if (uni) idx1 = last;
     }
     u64 res[8];
     float re[8];
@@ -199,25 +204,42 @@ __device__ __forceinline__ int warp_owner(uint32_t excl, uint32_t it) {
 }
 
 // Warp-cooperative recomputation of the outputs flagged in each lane's
-// `mask` (line s, chunk at xl0): the flagged outputs of the whole warp are
-// numbered and taken one per lane.  All 32 lanes must call.
+// `mask` (line s, chunk at xl0; bit 0 is never set): the flagged outputs of
+// the whole warp are numbered by output position r, then by lane, from one
+// ballot per position, and taken one per lane.  idx1 is the owner's common
+// operator of its flagged outputs (main_item), or -1 to look each one up.
+// All 32 lanes must call.
 template <int LT, class WS, class TP, bool kPairs>
-__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0,
+__device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int s, int xl0, int idx1,
                                             const typename WS::T* cur, typename WS::T* nxt, const float* srow,
                                             const float* qs, const typename TP::E* __restrict__ taps, int lane) {
-    uint32_t excl;
-    const uint32_t total = warp_enumerate(mask, lane, excl);
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t it = base + lane;
-        const int owner = warp_owner(excl, it);
-        const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
-        const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
+    uint32_t bal[8];
+    int pre[8];
+    int total = 0;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+        bal[r] = __ballot_sync(0xffffffffu, (mask >> r) & 1u);
+        pre[r] = total;
+        total += __popc(bal[r]);
+    }
+    for (int base = 0; base < total; base += 32) {
+        const int it = base + lane;
+        // position r of output number it: the last r whose numbering starts
+        // at or before it (a position with no outputs shares its start with
+        // the next one, so the last such r has it inside its range)
+        int r = 1;
+        uint32_t br = bal[1];
+        int pr = pre[1];
+#pragma unroll
+        for (int q = 2; q < 8; ++q)
+            if (pre[q] <= it) { r = q; br = bal[q]; pr = pre[q]; }
+        const int owner = it < total ? (int)__fns(br, 0, it - pr + 1) : 0;
         const int s_o = __shfl_sync(0xffffffffu, s, owner);
         const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
+        const int i1_o = __shfl_sync(0xffffffffu, idx1, owner);
         if (it < total) {
-            const int r = (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
             const int x = x0_o + r;
-            const int idx = op_index<kPairs>(qs[s_o], srow[x], g.nk);
+            const int idx = i1_o >= 0 ? i1_o : op_index<kPairs>(qs[s_o], srow[x], g.nk);
             WS::st1(nxt + (size_t)s_o * g.SP + phys(x + LT),
                     fir1<LT, WS, TP>(cur + (size_t)s_o * g.SP, x, taps + (size_t)idx * (LT + 1)));
         }
@@ -545,9 +567,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             uint32_t mask = 0;
-            if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps);
+            int idx1 = -1;
+            if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps, idx1);
             if (__any_sync(0xffffffffu, mask != 0u))
-                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, cur, nxt, srow, qz, taps, lane);
+                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, idx1, cur, nxt, srow, qz, taps, lane);
             if (__any_sync(0xffffffffu, issue_l || issue_r)) {
                 // the strips' outputs (main items, fixups of this warp) are in
                 // nxt; make them visible to the copy engine, then send
