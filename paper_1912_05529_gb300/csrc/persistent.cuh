@@ -481,9 +481,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     // Work items: (line, 8-output chunk), one per lane and round.  Chunks
     // within LT of a segment edge ("edge" chunks) read the halo, and their
     // outputs go to the neighbours' halos.  Halo exchange is point to point:
-    // after each round of items a warp sends its edge outputs with st.async
-    // (one output per lane), and a CTA waits on its own halo barrier of the
-    // step's parity before it reads its halo; neighbours can never be more
+    // after each round of items the warp that owns a line's edge chunks sends
+    // the line's halo strip (see the halo pushes above), and a CTA waits on
+    // its own halo barrier of the step's parity before it reads its halo;
+    // neighbours can never be more
     // than one step apart, so two parities suffice and no cluster-wide
     // barrier is needed.  One CTA barrier ends a depth step; the image row of
     // the step is summed right after it from the imaging buffer (overlapping
@@ -507,6 +508,41 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         const int j = item - s * NC;
         c = spread ? ((((j >> 3) & 3) * (NC >> 5) + (j >> 5)) << 3) + (j & 7) : j;
     };
+    // A lane's item of a round: line s, first output xl0 and flags: bit 0
+    // work (the chunk starts inside the segment), bits 1 / 2 the chunk reads
+    // and feeds the left / right halo, bits 3 / 4 it starts the line's left
+    // strip / ends its right strip, bits 8-15 its outputs that go to a
+    // neighbour's halo one by one (st.async form).  The push flags hold for
+    // steps whose outputs feed a further step.  Chunks c < E read the left
+    // halo and push to the left neighbour, chunks c >= NC - E the right ones
+    // (both also when the chunk lies beyond the line end and only pushes
+    // zeros).  Waiting for the neighbour's previous step on that side is what
+    // keeps the two CTAs within one step of each other, so a pusher waits
+    // even when it reads nothing.
+    auto item_state = [&](int item, int& s, int& xl0, uint32_t& f) {
+        s = 0;
+        xl0 = 0;
+        f = 0;
+        if (item >= n_items) return;
+        int c;
+        item_chunk(item, s, c);
+        xl0 = c << 3;
+        const bool need_l = sc.has_left && c < E, need_r = sc.has_right && c >= NC - E;
+        f = (xl0 < wv ? 1u : 0u) | (need_l ? 2u : 0u) | (need_r ? 4u : 0u);
+        if (strips) {
+            f |= (need_l && c == 0) ? 8u : 0u;
+            f |= (need_r && c == NC - 1) ? 16u : 0u;
+        } else if (need_l || need_r) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if ((need_l && xl0 + r < LT) || (need_r && xl0 + r >= W - LT)) f |= 256u << r;
+        }
+    };
+    // the first round's item is the same at every step
+    int s_first, xl0_first;
+    uint32_t f_first;
+    item_state(warp * 32 + lane, s_first, xl0_first, f_first);
+
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
         const T* cur = wave + (size_t)zb * m * SP;
@@ -531,33 +567,18 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         }
 
         for (int base = warp * 32; base < n_items; base += nwarps * 32) {
-            const int item = base + lane;
-            int s = 0, xl0 = 0;
-            bool work = false, need_l = false, need_r = false;
-            uint32_t pmask = 0;  // outputs of the item that go to a neighbour's halo (st.async form)
-            bool issue_l = false, issue_r = false;  // the item's chunk starts / ends its line's strip
-            if (item < n_items) {
-                int c;
-                item_chunk(item, s, c);
-                xl0 = c << 3;
-                work = xl0 < wv;
-                // Chunks c < E read the left halo and push to the left
-                // neighbour, chunks c >= NC - E the right ones (both also when
-                // the chunk lies beyond the line end and only pushes zeros).
-                // Waiting for the neighbour's previous step on that side is
-                // what keeps the two CTAs within one step of each other, so a
-                // pusher waits even when it reads nothing.
-                need_l = sc.has_left && c < E;
-                need_r = sc.has_right && c >= NC - E;
-                if (push && strips) {
-                    issue_l = need_l && c == 0;
-                    issue_r = need_r && c == NC - 1;
-                } else if (push && (need_l || need_r)) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r)
-                        if ((need_l && xl0 + r < LT) || (need_r && xl0 + r >= W - LT)) pmask |= 1u << r;
-                }
+            int s, xl0;
+            uint32_t f;
+            if (base == warp * 32) {
+                s = s_first;
+                xl0 = xl0_first;
+                f = f_first;
+            } else {
+                item_state(base + lane, s, xl0, f);
             }
+            const bool work = f & 1u, need_l = f & 2u, need_r = f & 4u;
+            const bool issue_l = push && (f & 8u), issue_r = push && (f & 16u);
+            const uint32_t pmask = push ? (f >> 8) & 0xffu : 0u;
             if (halo_wait) {
                 // the neighbours' outputs of step z-1 have landed in cur's halo
                 const bool wl = __any_sync(0xffffffffu, need_l), wr = __any_sync(0xffffffffu, need_r);
