@@ -259,22 +259,33 @@ __device__ __forceinline__ void fir8_shared_taps(const typename WS::T* __restric
 }
 
 // Eq. 1 for one output at local position x of a line, with taps tp[0..LT].
+// The window x-LT..x+LT (positions x + d, d = 0..2LT, of the line's padded
+// layout) is addressed from the 8-aligned block of x: with a = x mod 8,
+// phys(x + d) = 10 (x div 8) + a + d + 2 (d div 8) + 2 [a + (d mod 8) >= 8],
+// so every load is one of eight base registers plus a constant.
 template <int LT, class WS, class TP>
 __device__ __forceinline__ u64 fir1(const typename WS::T* __restrict__ line, int x,
                                     const typename TP::E* __restrict__ tp) {
+    const int a = x & 7;
+    const typename WS::T* bp = line + 10 * (x >> 3) + a;
+    int adj[8];
+    adj[0] = 0;
+#pragma unroll
+    for (int m = 1; m < 8; ++m) adj[m] = (a >= 8 - m) ? 2 : 0;
+    auto at = [&](int d) { return WS::ld1(bp + adj[d & 7] + d + 2 * (d >> 3)); };
     u64 hr, hi;
     TP::ld(tp, hr, hi);
-    const u64 c = WS::ld1(line + phys(x + LT));
+    const u64 c = at(LT);
     u64 A = f2_mul(hr, c), B = f2_mul(hi, c);
 #pragma unroll
     for (int n = 1; n <= LT; ++n) {
         TP::ld(tp + n, hr, hi);
-        const u64 t = f2_add(WS::ld1(line + phys(x + LT - n)), WS::ld1(line + phys(x + LT + n)));
+        const u64 t = f2_add(at(LT - n), at(LT + n));
         A = f2_fma(hr, t, A);
         B = f2_fma(hi, t, B);
     }
-    const float2 a = f2_unpack(A), b = f2_unpack(B);
-    return f2_pack(a.x - b.y, a.y + b.x);
+    const float2 av = f2_unpack(A), bv = f2_unpack(B);
+    return f2_pack(av.x - bv.y, av.y + bv.x);
 }
 
 }  // namespace fxmig_impl
