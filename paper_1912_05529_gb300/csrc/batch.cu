@@ -45,8 +45,9 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, int v) {
 }
 
 template <int LT>
-__device__ __forceinline__ void run_item_lt(const MigrateArgs& a, int g, unsigned char* smem) {
-    run_group<LT, WsF32, TapF32>(a, g, smem);
+__device__ __forceinline__ void run_item_lt(const MigrateArgs& a, int g, unsigned char* smem, int part,
+                                            bool accumulate) {
+    run_group<LT, WsF32, TapF32>(a, g, smem, part, accumulate);
 }
 
 __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_migrate_batch(const __grid_constant__ BatchArgs b) {
@@ -73,17 +74,16 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_migrate_batch(const __g
         const int p = item - b.item_base[k];  // the line's stream
         const int g0 = (int)(((long long)p * L.a.G) / L.P), g1 = (int)(((long long)(p + 1) * L.a.G) / L.P);
         for (int g = g0; g < g1; ++g) {
-            MigrateArgs a = L.a;
-            a.part_fixed = 1;
-            a.part = p;
-            a.accumulate = g > g0;
+            // the groups of stream p add their rows into partial image p
+            // (the line's arguments are read in place from the parameters)
+            const bool acc = g > g0;
             switch (L.LT) {
-                case 4: run_item_lt<4>(a, g, smem); break;
-                case 8: run_item_lt<8>(a, g, smem); break;
-                case 12: run_item_lt<12>(a, g, smem); break;
-                case 16: run_item_lt<16>(a, g, smem); break;
-                case 17: run_item_lt<17>(a, g, smem); break;
-                case 20: run_item_lt<20>(a, g, smem); break;
+                case 4: run_item_lt<4>(L.a, g, smem, p, acc); break;
+                case 8: run_item_lt<8>(L.a, g, smem, p, acc); break;
+                case 12: run_item_lt<12>(L.a, g, smem, p, acc); break;
+                case 16: run_item_lt<16>(L.a, g, smem, p, acc); break;
+                case 17: run_item_lt<17>(L.a, g, smem, p, acc); break;
+                case 20: run_item_lt<20>(L.a, g, smem, p, acc); break;
                 default: break;
             }
             // the next group reuses the shared memory: every CTA of the

@@ -34,8 +34,6 @@ struct MigrateArgs {
     int W, C, G, lines, tma_ok;
     int cwarps, ewarps;     // persistent: interior compute warps, edge warps
     int img;                // persistent: imaging buffer in shared memory (persistent_layout)
-    int part_fixed, part;   // partial image written: group g's own (0) or number `part` (1)
-    int accumulate;         // add the group's rows to the partial image instead of storing them
     // operators per (frequency, distinct slowness) pair instead of the table
     // (kPairs): `slow` holds every point's pair index within its row, `taps`
     // the operators of rows [pair_z0, ...) in pair order
@@ -306,12 +304,14 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 }
 
 // The whole depth loop of frequency group g of problem a, on the CTAs of one
-// cluster (all of them call it with the same a and g).  smem is the CTA's
-// dynamic shared memory (persistent_layout).  On return every mbarrier used
+// cluster (all of them call it with the same arguments).  smem is the CTA's
+// dynamic shared memory (persistent_layout).  The group's image rows go to
+// partial image `part`, added to what it holds when `accumulate` is set.  On return every mbarrier used
 // is invalidated and no copy or remote store is in flight, so the memory can
 // hold the next group.
 template <int LT, class WS, class TP, bool kPairs = false>
-__device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned char* smem) {
+__device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned char* smem, int part,
+                                          bool accumulate) {
     typedef typename WS::T T;
     const typename TP::E* __restrict__ taps_all = static_cast<const typename TP::E*>(a.taps);
     const int W = a.W, m = a.lines, C = a.C;
@@ -410,7 +410,6 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     // depth z, by threads t = 0..nt-1: from the imaging buffer after the step
     // barrier, or (no buffer) from the step's input wavefield, which nobody
     // writes during the step, before the barrier
-    const int part = a.part_fixed ? a.part : g;
     auto reduce_image_row = [&](int z, const T* cur, int t, int nt) {
         float* dst = a.partials + ((size_t)part * a.nz + z) * a.nx + x0;
         if (img) {
@@ -422,7 +421,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                     acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
                 }
                 if (x + 4 <= wv && (a.nx & 3) == 0) {
-                    if (a.accumulate) {
+                    if (accumulate) {
                         const float4 o = *reinterpret_cast<const float4*>(dst + x);
                         acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
                     }
@@ -430,7 +429,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 } else {
                     for (int i = 0; i < 4 && x + i < wv; ++i) {
                         const float t = i == 0 ? acc.x : i == 1 ? acc.y : i == 2 ? acc.z : acc.w;
-                        dst[x + i] = a.accumulate ? dst[x + i] + t : t;
+                        dst[x + i] = accumulate ? dst[x + i] + t : t;
                     }
                 }
             }
@@ -438,7 +437,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             for (int x = t; x < wv; x += nt) {
                 float acc = 0.f;
                 for (int s = 0; s < mg; ++s) acc += WS::to_f2(cur[(size_t)s * SP + phys(x + LT)]).x;
-                dst[x] = a.accumulate ? dst[x] + acc : acc;
+                dst[x] = accumulate ? dst[x] + acc : acc;
             }
         }
     };
@@ -466,17 +465,14 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         sc.bar_left[b] = sc.has_left ? map_cluster_rank(&hbar[2 + b], rank - 1) : 0u;   // its right halo
         sc.bar_right[b] = sc.has_right ? map_cluster_rank(&hbar[b], rank + 1) : 0u;     // its left halo
     }
-    // Halo pushes: one strip per line and side, sent by the warp that owns
-    // the strip's chunks (the spread mapping below keeps them in one warp)
-    // when a strip and its landing place have the same 16-byte alignment;
-    // else one st.async per output.  Bytes each halo barrier phase receives:
-    // the strips of every line (pads included), or LT outputs of every line.
+    // Halo pushes: one strip per line and side, sent whole by the warp that
+    // owns the strip's chunks when they fall in one warp's round and a strip
+    // and its landing place have the same 16-byte alignment; else one
+    // st.async per output (bytes per barrier phase below).
     typedef HaloStrips<LT> HS;
     const int physW = W + 2 * (W >> 3);
-    const bool strips = C > 1 && (W & 7) == 0 && ((W >> 3) & 31) == 0 && (physW * WS::kBytes) % 16 == 0;
+    const bool strips = C > 1 && (W & 7) == 0 && (physW * WS::kBytes) % 16 == 0;
     const uint32_t kB = (uint32_t)WS::kBytes;
-    const uint32_t halo_bytes_l = (uint32_t)mg * (strips ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB);
-    const uint32_t halo_bytes_r = (uint32_t)mg * (strips ? (uint32_t)HS::kLeftN * kB : (uint32_t)LT * kB);
 
     // Work items: (line, 8-output chunk), one per lane and round.  Chunks
     // within LT of a segment edge ("edge" chunks) read the halo, and their
@@ -498,6 +494,18 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
     const bool magic_ok = NC >= 2 && (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
     const bool spread = (NC & 31) == 0;  // lines of whole warps of items
+    // Line s's left (right) strip goes whole when its chunks c < E
+    // (c >= NC - E) are items of one 32-item block, i.e. of one warp's round:
+    // always with the spread mapping below, else unless the line's items
+    // cross a block boundary there.  Bytes each halo barrier phase receives:
+    // per line the neighbour's strip (pads included) or its LT outputs.
+    auto left_whole = [&](int s) { return strips && (spread || (((s * NC) & 31) + E <= 32)); };
+    auto right_whole = [&](int s) { return strips && (spread || (((s * NC + NC - 1) & 31) + 1 >= E)); };
+    uint32_t halo_bytes_l = 0, halo_bytes_r = 0;
+    for (int s = 0; s < mg; ++s) {
+        halo_bytes_l += right_whole(s) ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB;
+        halo_bytes_r += left_whole(s) ? (uint32_t)HS::kLeftN * kB : (uint32_t)LT * kB;
+    }
     // line s and chunk c of a valid item.  With `spread`, a warp's 32 items
     // of a line, j = 32a + 8q + r, take chunk 8 (q NC/32 + a) + r, so each
     // warp covers four blocks of 8 chunks a quarter of the line apart
@@ -529,13 +537,13 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         xl0 = c << 3;
         const bool need_l = sc.has_left && c < E, need_r = sc.has_right && c >= NC - E;
         f = (xl0 < wv ? 1u : 0u) | (need_l ? 2u : 0u) | (need_r ? 4u : 0u);
-        if (strips) {
-            f |= (need_l && c == 0) ? 8u : 0u;
-            f |= (need_r && c == NC - 1) ? 16u : 0u;
-        } else if (need_l || need_r) {
+        const bool lw = left_whole(s), rw = right_whole(s);
+        f |= (need_l && lw && c == 0) ? 8u : 0u;
+        f |= (need_r && rw && c == NC - 1) ? 16u : 0u;
+        if ((need_l && !lw) || (need_r && !rw)) {
 #pragma unroll
             for (int r = 0; r < 8; ++r)
-                if ((need_l && xl0 + r < LT) || (need_r && xl0 + r >= W - LT)) f |= 256u << r;
+                if ((need_l && !lw && xl0 + r < LT) || (need_r && !rw && xl0 + r >= W - LT)) f |= 256u << r;
         }
     };
     // the first round's item is the same at every step
@@ -644,7 +652,8 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
 template <int LT, class WS, class TP, bool kPairs = false>
 __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_group<LT, WS, TP, kPairs>(a, (int)(blockIdx.x / a.C), smem);
+    const int g = (int)(blockIdx.x / a.C);
+    run_group<LT, WS, TP, kPairs>(a, g, smem, g, false);
 }
 
 

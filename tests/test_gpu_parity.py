@@ -178,3 +178,24 @@ def test_migrate_widths_not_multiple_of_four(fx, nx, launch):
     tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if not (launch and launch.get("precision")) else (1e-2, 1e-2)
     assert rel_l2(slabs[-1], P_ref) < tol_s
     assert rel_l2(image, img_ref) < tol_i
+
+
+@pytest.mark.parametrize("L,prec", [(8, "FP32"), (12, "FP32"), (17, "FP32"), (20, "FP32"),
+                                    (12, "FP16_SPLIT"), (17, "FP16_SPLIT")])
+def test_halo_strips(fx, L, prec):
+    # 1000 traces over clusters of 4: segments of 256 traces (the last one
+    # partly beyond the line end), whose edge warps send each line's halo
+    # strip as one piece: a bulk copy of its 16-byte aligned middle and
+    # single stores for the slots around it (odd L; 4-byte values)
+    w = small_layered(nx=1000, nz=24, L=L, seed=11, name="layered_1000")
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    d = desc_of(fx, w, pr["k_max"])
+    launch = fx.Launch(mode=1, cluster=4, precision=getattr(fx, "FXMIG_PREC_" + prec))
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch, [0, 9, w.nz])
+    P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if prec == "FP32" else (1e-2, 1e-2)
+    assert rel_l2(slabs[-1], P_ref) < tol_s
+    assert rel_l2(image, img_ref) < tol_i
