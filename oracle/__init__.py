@@ -12,7 +12,7 @@ Implementation of Poststack Depth Migration", arXiv 1912.05529.
 
 Steps, in the order of Algorithm 1, and what each follows:
 
-* ``band_dft``            Algorithm 1 "Fourier transform along the t-axis";
+* ``band_dft``            Algorithm 1, time-to-frequency step;
                           Sec. III.  Naive DFT, e^{-i w t}, no scaling, band
                           bins only.
 * ``design_operators``    Sec. II (design as an optimisation between short and

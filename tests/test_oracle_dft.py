@@ -1,4 +1,4 @@
-"""Pins of the oracle's t -> f transform (Algorithm 1, Fourier transform along t)."""
+"""Pins of the oracle's t -> f transform (Algorithm 1, time-to-frequency step)."""
 import math
 
 import numpy as np
