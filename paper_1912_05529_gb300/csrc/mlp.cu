@@ -8,8 +8,8 @@
 // Flat parameter order (each row-major, W[out][in]):
 //     W1[64][1] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[NO][64] b4[NO].
 //
-// Arithmetic: the 64-wide layers run on the tensor cores as
-// mma.sync.m16n8k16 with BF16 operands and FP32 accumulation.  Every operand
+// Arithmetic: the 64-wide layers run on the tensor cores with BF16 operands
+// and FP32 accumulation (training: mma.sync.m16n8k16; inference: tcgen05).  Every operand
 // is split into two BF16 terms (v = hi + lo, lo = bf16(v - hi)) and a product
 // is formed from three MMAs (hi*hi + hi*lo + lo*hi), which keeps about 16
 // significant bits per operand: a single BF16 rounding (8 bits) leaves tap
@@ -22,9 +22,10 @@
 //   k_mlp_adam   sums the CTA partials in ascending order and applies Adam to
 //                the FP32 master parameters (or, for gradient checks, writes
 //                the summed gradient).
-// Inference (k_mlp_infer): one warp per 16 samples, activations kept in MMA
-// fragments in registers (the accumulator layout of one layer is the operand
-// layout of the next), weights in shared memory.
+// Inference (k_mlp_infer_tc): the 64-wide layers on the 5th-generation tensor
+// cores (tcgen05.mma, accumulator in tensor memory) for tiles of 128 samples,
+// the same three-term split; GELU and the split of each activation on the
+// CUDA cores between the layers.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -37,7 +38,6 @@ constexpr int kLd = 72;        // padded shared-memory row (bf16): conflict-free
 constexpr int kLdY = 40;       // padded row of the output-gradient tile
 constexpr int kTrainRows = 64;
 constexpr int kTrainWarps = 4;
-constexpr int kInferWarps = 8;
 
 __host__ __device__ inline int nout_of(int L) { return 2 * (L + 1); }
 __host__ __device__ inline int n_params(int no) { return 4 * kH + 2 * kH * kH + no * kH + no; }
@@ -482,122 +482,259 @@ __device__ __forceinline__ float block_input(const InferArgs& a, const BlockTabl
     return fminf(fmaxf(x, 0.f), 1.f);  // the network is defined on [0, 1]; NaN maps to 0
 }
 
-// Layer 1 (scalar input) straight into split A fragments of layer 2:
-// lane holds rows g, g+8 and columns 16 kt + 2t (+1, +8, +9).
-__device__ __forceinline__ void infer_layer1(const WeightSmem& S, float xg, float xg8, int t,
-                                             uint32_t (&ah)[4][4], uint32_t (&al)[4][4]) {
+// ---------------------------------------------------- inference, tcgen05 form
+// The three 64-wide layers as tcgen05 MMAs (M = 128 samples, N = 64 or 32,
+// K = 16 per instruction, BF16 operands from shared memory, FP32 accumulator
+// in tensor memory), with the same three-term split as above.  A CTA of 8
+// warps takes 128 samples per tile; warp w owns TMEM lanes 32 (w mod 4) (its
+// samples) and columns 32 (w div 4) of the 64 (its half of each layer).  One
+// thread issues the MMAs; their completion arrives on an mbarrier, and the
+// warps read the accumulator with tcgen05.ld, add the bias, apply GELU and
+// write the split activations back as the next layer's A operand.
+//
+// Operand layout in shared memory (K-major, no swizzle): a [rows][64] BF16
+// matrix is cut into core matrices of 8 rows x 8 elements (16 bytes a row,
+// 128 bytes each), stored K-group-fastest: core matrix (r/8, k/8) at
+// ((r/8) * 8 + k/8) * 128 bytes.  Core matrices adjacent in K are 128 bytes
+// apart (leading offset), adjacent in rows 1024 bytes (stride offset).
+constexpr int kTcRows = 128;   // samples per tile = TMEM lanes
+constexpr int kTcWarps = 8;
+constexpr int kTcCols = 64;    // TMEM columns (FP32 accumulator of one layer)
+
+// GELU (erf form) a * Phi(a) for inference: Phi from erfc(x), x = |a| / sqrt 2,
+// by Hastings' rational approximation (Abramowitz & Stegun 7.1.26):
+// erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
+// absolute error <= 1.5e-7 for x >= 0; Phi(a) = 1 - erfc(x) / 2 for a >= 0,
+// erfc(x) / 2 below.  Hardware reciprocal and exponential keep it to about a
+// dozen instructions, against the split-BF16 operands' 1e-5 relative error.
+__device__ __forceinline__ float gelu_fast(float a) {
+    const float x = fabsf(a) * 0.70710678118654752f;
+    const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                 0.254829592f);
+    const float half_erfc = 0.5f * poly * __expf(-x * x);
+    return a * (a >= 0.f ? 1.f - half_erfc : half_erfc);
+}
+
+__device__ __forceinline__ int cm_index(int r, int k) { return (((r >> 3) * 8 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7); }
+
+struct TcSmem {
+    bf16 W2h[kH * kH], W2l[kH * kH], W3h[kH * kH], W3l[kH * kH];  // [out][in], core-matrix layout
+    bf16 W4h[kMlpMaxOut * kH], W4l[kMlpMaxOut * kH];
+    bf16 Ah[kTcRows * kH], Al[kTcRows * kH];                       // activations [sample][in]
+    float W1[kH], b1[kH], b2[kH], b3[kH], b4[kMlpMaxOut];
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__device__ void load_weights_tc(TcSmem& S, const float* __restrict__ p, int no) {
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+        const int r = i / kH, c = i - r * kH, j = cm_index(r, c);
+        split(__ldg(p + oW2() + i), S.W2h[j], S.W2l[j]);
+        split(__ldg(p + oW3() + i), S.W3h[j], S.W3l[j]);
+    }
+    for (int i = threadIdx.x; i < kMlpMaxOut * kH; i += blockDim.x) {
+        const int r = i / kH, c = i - r * kH, j = cm_index(r, c);
+        split(r < no ? __ldg(p + oW4() + i) : 0.f, S.W4h[j], S.W4l[j]);
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        S.W1[i] = p[oW1() + i];
+        S.b1[i] = p[ob1() + i];
+        S.b2[i] = p[ob2() + i];
+        S.b3[i] = p[ob3() + i];
+    }
+    for (int i = threadIdx.x; i < kMlpMaxOut; i += blockDim.x) S.b4[i] = i < no ? p[ob4(no) + i] : 0.f;
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (row-group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 32 lanes x 32 bits, 16 consecutive columns starting at taddr (the warp's lanes).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One layer's MMAs: D[128][n] = A[128][64] W[n][64]^T from the split terms,
+// four K steps of 16 (two core matrices, 256 bytes) each; the small terms of
+// each K step first, as in mma3.
+__device__ __forceinline__ void tc_layer(uint32_t d, const bf16* Ah, const bf16* Al, const bf16* Wh, const bf16* Wl,
+                                         int n) {
+    const uint32_t idesc = tc_idesc(n);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {  // a0: (g, c), a1: (g+8, c), a2: (g, c+8), a3: (g+8, c+8)
-            const int c = kt * 16 + 2 * t + ((q & 2) ? 8 : 0);
-            const float xr = (q & 1) ? xg8 : xg;
-            const float a0 = S.W1[c] * xr + S.b1[c], a1 = S.W1[c + 1] * xr + S.b1[c + 1];
-            split_pack(a0 * gelu_cdf(a0), a1 * gelu_cdf(a1), ah[kt][q], al[kt][q]);
-        }
+    for (int kk = 0; kk < kH / 16; ++kk) {
+        const uint32_t off = (uint32_t)kk * 256u;
+        const uint64_t ah = tc_sdesc(reinterpret_cast<const unsigned char*>(Ah) + off, 128, 1024);
+        const uint64_t al = tc_sdesc(reinterpret_cast<const unsigned char*>(Al) + off, 128, 1024);
+        const uint64_t bh = tc_sdesc(reinterpret_cast<const unsigned char*>(Wh) + off, 128, 1024);
+        const uint64_t bl = tc_sdesc(reinterpret_cast<const unsigned char*>(Wl) + off, 128, 1024);
+        tc_mma(d, al, bh, idesc, kk > 0 ? 1u : 0u);
+        tc_mma(d, ah, bl, idesc, 1u);
+        tc_mma(d, ah, bh, idesc, 1u);
     }
 }
 
-// Hidden layer on register fragments: C = A W^T + b, then gelu and the split
-// A fragments of the next layer (C tile 2kt gives a0/a1, tile 2kt+1 a2/a3).
-__device__ __forceinline__ void infer_hidden(const bf16* Wh, const bf16* Wl, const float* b, int lane,
-                                             uint32_t (&ah)[4][4], uint32_t (&al)[4][4]) {
-    const int t = lane & 3;
-    float c[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            uint32_t bh[2], bl[2];
-            ldb_nmajor(Wh, kLd, kt * 16, nt * 8, lane, bh);
-            ldb_nmajor(Wl, kLd, kt * 16, nt * 8, lane, bl);
-            mma3(c[nt], ah[kt], al[kt], bh, bl);
-        }
+// One layer on the tensor cores: the activations every thread wrote become
+// visible to the MMAs, thread 0 issues them, everyone waits for their
+// completion (bounded).  Returns false, the same in every thread, when the
+// wait gave up.
+__device__ __forceinline__ bool tc_run(TcSmem& S, int tid, uint32_t tmem, const bf16* Wh, const bf16* Wl, int n,
+                                       uint32_t phase) {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        tc_fence_after();
+        tc_layer(tmem, S.Ah, S.Al, Wh, Wl, n);
+        tc_commit(&S.bar);
     }
+    const bool done = mbar_wait_bounded(&S.bar, phase & 1u, kWaitPolls);
+    tc_fence_after();
+    return !__syncthreads_or(done ? 0 : 1);
+}
+
+// Thread's sample row m, columns c0..c0+31 of an activation row as split
+// BF16 in the core-matrix layout (four 16-byte stores per term).
+__device__ __forceinline__ void tc_store_act(TcSmem& S, int m, int c0, const float (&h)[32]) {
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int col = nt * 8 + 2 * t;
-        const float b0 = b[col], b1 = b[col + 1];
-        float v[4];
+    for (int j = 0; j < 4; ++j) {
+        uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float a = c[nt][i] + ((i & 1) ? b1 : b0);
-            v[i] = a * gelu_cdf(a);
-        }
-        const int kt = nt >> 1, hiq = (nt & 1) ? 2 : 0;
-        split_pack(v[0], v[1], ah[kt][hiq], al[kt][hiq]);          // row g
-        split_pack(v[2], v[3], ah[kt][hiq + 1], al[kt][hiq + 1]);  // row g + 8
+        for (int e = 0; e < 4; ++e) split_pack(h[8 * j + 2 * e], h[8 * j + 2 * e + 1], hi[e], lo[e]);
+        const int idx = cm_index(m, c0 + 8 * j);
+        *reinterpret_cast<uint4*>(S.Ah + idx) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(S.Al + idx) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
-__global__ void __launch_bounds__(kInferWarps * 32) k_mlp_infer(const InferArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    WeightSmem& S = *reinterpret_cast<WeightSmem*>(smraw);
-    BlockTables& T = *reinterpret_cast<BlockTables*>(smraw + sizeof(WeightSmem));
-    load_weights(S, a.params, a.no);
+// Hidden layer epilogue: bias, GELU and the split A operand of the next layer
+// for the thread's sample and its 32 columns.
+__device__ __forceinline__ void tc_hidden_epilogue(TcSmem& S, uint32_t tcol, int m, int c0, const float* b) {
+    float h[32];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float v[16];
+        tc_ld16(tcol + 16 * half, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            h[16 * half + i] = gelu_fast(v[i] + b[c0 + 16 * half + i]);
+        }
+    }
+    tc_store_act(S, m, c0, h);
+}
+
+__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs a) {
+    extern __shared__ __align__(16) unsigned char smtc[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smtc);
+    BlockTables& T = *reinterpret_cast<BlockTables*>(smtc + sizeof(TcSmem));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = 32 * (warp & 3) + lane;  // the thread's sample row (TMEM lane)
+    const int c0 = 32 * (warp >> 2);       // its 32 columns of a hidden layer
+    load_weights_tc(S, a.params, a.no);
     long long total = a.n;
     if (!a.kv) {
         const long long first = a.base[a.z0];
-        for (int i = threadIdx.x; i <= a.z1 - a.z0; i += blockDim.x) {
+        for (int i = tid; i <= a.z1 - a.z0; i += blockDim.x) {
             T.base[i] = a.base[a.z0 + i] - first;
             if (i < a.z1 - a.z0) T.cnt[i] = a.cnt[a.z0 + i];
         }
-        for (int j = threadIdx.x; j < a.nw; j += blockDim.x) T.q[j] = q_of_line_mlp(a.i0, j, a.nt, a.dt, a.inv_kmax);
+        for (int j = tid; j < a.nw; j += blockDim.x) T.q[j] = q_of_line_mlp(a.i0, j, a.nt, a.dt, a.inv_kmax);
         total = a.base[a.z1] - first;
     }
+    if (tid == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&S.tmem)), "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // weights (generic stores) become visible to the tensor cores' reads
+    fence_proxy_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const long long tiles = (total + 15) / 16;
-    for (long long tile = (long long)blockIdx.x * kInferWarps + warp; tile < tiles;
-         tile += (long long)gridDim.x * kInferWarps) {
-        const long long r_g = tile * 16 + g, r_g8 = r_g + 8;
-        float xg = 0.f, xg8 = 0.f;
-        if (a.kv) {
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // the warp's lanes, column 0
+    uint32_t phase = 0;
+    const long long tiles = (total + kTcRows - 1) / kTcRows;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long r = tile * kTcRows + m;
+        float x = 0.f;
+        if (r < total) {
             // the network is defined on [0, 1]; NaN maps to 0
-            if (r_g < total) xg = fminf(fmaxf((float)(a.kv[r_g] * a.inv_kmax), 0.f), 1.f);
-            if (r_g8 < total) xg8 = fminf(fmaxf((float)(a.kv[r_g8] * a.inv_kmax), 0.f), 1.f);
-        } else {
-            if (r_g < total) xg = block_input(a, T, r_g);
-            if (r_g8 < total) xg8 = block_input(a, T, r_g8);
+            x = a.kv ? fminf(fmaxf((float)(a.kv[r] * a.inv_kmax), 0.f), 1.f) : block_input(a, T, r);
         }
-        uint32_t ah[4][4], al[4][4];
-        infer_layer1(S, xg, xg8, t, ah, al);
-        infer_hidden(S.W2h, S.W2l, S.b2, lane, ah, al);
-        infer_hidden(S.W3h, S.W3l, S.b3, lane, ah, al);
-        // output layer: tile nt holds taps 4 nt + t as (Re, Im) for rows g, g+8
+        {
+            float h[32];
 #pragma unroll
-        for (int nt = 0; nt < kMlpMaxOut / 8; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                uint32_t bh[2], bl[2];
-                ldb_nmajor(S.W4h, kLd, kt * 16, nt * 8, lane, bh);
-                ldb_nmajor(S.W4l, kLd, kt * 16, nt * 8, lane, bl);
-                mma3(c, ah[kt], al[kt], bh, bl);
+            for (int i = 0; i < 32; ++i) {
+                h[i] = gelu_fast(S.W1[c0 + i] * x + S.b1[c0 + i]);
             }
-            const int tap = 4 * nt + t;
-            if (tap <= a.L) {
-                const float hr0 = c[0] + S.b4[2 * tap], hi0 = c[1] + S.b4[2 * tap + 1];
-                const float hr8 = c[2] + S.b4[2 * tap], hi8 = c[3] + S.b4[2 * tap + 1];
-                if (a.kv) {
-                    if (r_g < total) a.taps_pub[r_g * (a.L + 1) + tap] = make_float2(hr0, hi0);
-                    if (r_g8 < total) a.taps_pub[r_g8 * (a.L + 1) + tap] = make_float2(hr8, hi8);
-                } else {
-                    if (r_g < total) a.taps_k[r_g * (a.LT + 1) + tap] = make_float4(hr0, hr0, hi0, hi0);
-                    if (r_g8 < total) a.taps_k[r_g8 * (a.LT + 1) + tap] = make_float4(hr8, hr8, hi8, hi8);
+            tc_store_act(S, m, c0, h);
+        }
+        if (!tc_run(S, tid, tmem, S.W2h, S.W2l, kH, phase++)) break;
+        tc_hidden_epilogue(S, tlane + (uint32_t)c0, m, c0, S.b2);
+        if (!tc_run(S, tid, tmem, S.W3h, S.W3l, kH, phase++)) break;
+        tc_hidden_epilogue(S, tlane + (uint32_t)c0, m, c0, S.b3);
+        if (!tc_run(S, tid, tmem, S.W4h, S.W4l, kMlpMaxOut, phase++)) break;
+        {
+            // output columns 16 (warp div 4) .. +15: taps 8 (warp div 4) .. +7
+            float v[16];
+            const int o0 = 16 * (warp >> 2);
+            tc_ld16(tlane + (uint32_t)o0, v);
+            if (r < total) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int tap = o0 / 2 + i;
+                    const float hr = v[2 * i] + S.b4[o0 + 2 * i], hi = v[2 * i + 1] + S.b4[o0 + 2 * i + 1];
+                    if (a.kv) {
+                        if (tap <= a.L) a.taps_pub[r * (a.L + 1) + tap] = make_float2(hr, hi);
+                    } else if (tap <= a.LT) {
+                        // taps beyond L of the compiled operator length are zero
+                        a.taps_k[r * (a.LT + 1) + tap] = tap <= a.L ? make_float4(hr, hr, hi, hi)
+                                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
             }
         }
-        if (!a.kv && a.LT > a.L) {  // zero taps L+1..LT of the compiled operator length
-            const int nzt = a.LT - a.L;
-            for (int i = lane; i < 16 * nzt; i += 32) {
-                const long long r = tile * 16 + i / nzt;
-                if (r < total) a.taps_k[r * (a.LT + 1) + a.L + 1 + i % nzt] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
+        tc_fence_before();  // this tile's accumulator reads precede the next tile's MMAs
     }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols) : "memory");
+    }
+    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(&S.bar)) : "memory");
 }
 
 static int sm_count() {
@@ -608,15 +745,16 @@ static int sm_count() {
 }
 
 static cudaError_t launch_infer(const InferArgs& a, long long max_total, cudaStream_t s) {
-    const size_t smem = sizeof(WeightSmem) + (a.kv ? 0 : block_tables_bytes(a.nw));
-    cudaError_t e = ensure_smem(k_mlp_infer, smem);
+    // tcgen05 form: two CTAs of 128 samples per SM (73 KB of shared memory
+    // and 64 TMEM columns each)
+    const size_t smem = sizeof(TcSmem) + (a.kv ? 0 : block_tables_bytes(a.nw));
+    cudaError_t e = ensure_smem(k_mlp_infer_tc, smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (max_total + 15) / 16;
-    long long grid = (tiles + kInferWarps - 1) / kInferWarps;
+    long long grid = (max_total + kTcRows - 1) / kTcRows;
     const long long cap = (long long)sm_count() * 2;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    k_mlp_infer<<<(unsigned)grid, kInferWarps * 32, smem, s>>>(a);
+    k_mlp_infer_tc<<<(unsigned)grid, kTcWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,7 @@
 //   k_pair_offsets  first (frequency, value) pair of every row (prefix sums
 //                   of nw * count);
 //   per block of Zc rows: the network writes the operators of all pairs of
-//   the block (k_mlp_infer), then the block's depth steps run in the
+//   the block (k_mlp_infer_tc), then the block's depth steps run in the
 //   persistent form (the frequency lines stay in shared memory for the
 //   block's rows; the staged rows hold every point's pair index instead of
 //   its slowness), or, when rows cannot be staged by TMA (nx not a multiple
