@@ -485,12 +485,15 @@ __device__ __forceinline__ float block_input(const InferArgs& a, const BlockTabl
 // ---------------------------------------------------- inference, tcgen05 form
 // The three 64-wide layers as tcgen05 MMAs (M = 128 samples, N = 64 or 32,
 // K = 16 per instruction, BF16 operands from shared memory, FP32 accumulator
-// in tensor memory), with the same three-term split as above.  A CTA of 8
-// warps takes 128 samples per tile; warp w owns TMEM lanes 32 (w mod 4) (its
-// samples) and columns 32 (w div 4) of the 64 (its half of each layer).  One
-// thread issues the MMAs; their completion arrives on an mbarrier, and the
-// warps read the accumulator with tcgen05.ld, add the bias, apply GELU and
-// write the split activations back as the next layer's A operand.
+// in tensor memory), with the same three-term split as above.  A CTA holds
+// two groups of 8 warps that work on tiles of their own (the MMAs of one
+// group's layer run while the other group computes its GELUs); a group takes
+// 128 samples per tile, its warp w owns TMEM lanes 32 (w mod 4) (its samples)
+// and columns 32 ((w div 4) mod 2) of its 64 (its half of each layer).  One
+// thread of the group issues the MMAs; their completion arrives on the
+// group's mbarrier, and the warps read the accumulator with tcgen05.ld, add
+// the bias, apply GELU and write the split activations back as the next
+// layer's A operand.  A group synchronises on its own named barrier.
 //
 // Operand layout in shared memory (K-major, no swizzle): a [rows][64] BF16
 // matrix is cut into core matrices of 8 rows x 8 elements (16 bytes a row,
@@ -498,8 +501,9 @@ __device__ __forceinline__ float block_input(const InferArgs& a, const BlockTabl
 // ((r/8) * 8 + k/8) * 128 bytes.  Core matrices adjacent in K are 128 bytes
 // apart (leading offset), adjacent in rows 1024 bytes (stride offset).
 constexpr int kTcRows = 128;   // samples per tile = TMEM lanes
-constexpr int kTcWarps = 8;
-constexpr int kTcCols = 64;    // TMEM columns (FP32 accumulator of one layer)
+constexpr int kTcGroups = 2;
+constexpr int kTcWarps = 8 * kTcGroups;
+constexpr int kTcCols = 64 * kTcGroups;  // TMEM columns: one FP32 accumulator of a layer per group
 
 // GELU (erf form) a * Phi(a) for inference: Phi from erfc(x), x = |a| / sqrt 2,
 // by Hastings' rational approximation (Abramowitz & Stegun 7.1.26):
@@ -522,9 +526,9 @@ __device__ __forceinline__ int cm_index(int r, int k) { return (((r >> 3) * 8 + 
 struct TcSmem {
     bf16 W2h[kH * kH], W2l[kH * kH], W3h[kH * kH], W3l[kH * kH];  // [out][in], core-matrix layout
     bf16 W4h[kMlpMaxOut * kH], W4l[kMlpMaxOut * kH];
-    bf16 Ah[kTcRows * kH], Al[kTcRows * kH];                       // activations [sample][in]
+    bf16 Ah[kTcGroups][kTcRows * kH], Al[kTcGroups][kTcRows * kH];  // activations [sample][in]
     float W1[kH], b1[kH], b2[kH], b3[kH], b4[kMlpMaxOut];
-    uint64_t bar;
+    uint64_t bar[kTcGroups];
     uint32_t tmem;
 };
 
@@ -602,42 +606,55 @@ __device__ __forceinline__ void tc_layer(uint32_t d, const bf16* Ah, const bf16*
     }
 }
 
-// One layer on the tensor cores: the activations every thread wrote become
-// visible to the MMAs, thread 0 issues them, everyone waits for their
-// completion (bounded).  Returns false, the same in every thread, when the
-// wait gave up.
-__device__ __forceinline__ bool tc_run(TcSmem& S, int tid, uint32_t tmem, const bf16* Wh, const bf16* Wl, int n,
-                                       uint32_t phase) {
+// Named barrier of group g (id 1 + g, its 256 threads); the OR variant
+// returns whether any thread of the group passed true.
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(256) : "memory");
+}
+__device__ __forceinline__ bool group_any(int g, bool v) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, %3, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"(v ? 1u : 0u), "r"(1 + g), "r"(256) : "memory");
+    return r != 0;
+}
+
+// One layer of group g on the tensor cores: the activations its threads
+// wrote become visible to the MMAs, its first thread issues them, the group
+// waits for their completion (bounded).  Returns false, the same in every
+// thread of the group, when the wait gave up.
+__device__ __forceinline__ bool tc_run(TcSmem& S, int g, bool issuer, uint32_t dcol, const bf16* Wh, const bf16* Wl,
+                                       int n, uint32_t phase) {
     fence_proxy_async_smem();
     tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
+    group_sync(g);
+    if (issuer) {
         tc_fence_after();
-        tc_layer(tmem, S.Ah, S.Al, Wh, Wl, n);
-        tc_commit(&S.bar);
+        tc_layer(dcol, S.Ah[g], S.Al[g], Wh, Wl, n);
+        tc_commit(&S.bar[g]);
     }
-    const bool done = mbar_wait_bounded(&S.bar, phase & 1u, kWaitPolls);
+    const bool done = mbar_wait_bounded(&S.bar[g], phase & 1u, kWaitPolls);
     tc_fence_after();
-    return !__syncthreads_or(done ? 0 : 1);
+    return !group_any(g, !done);
 }
 
 // Thread's sample row m, columns c0..c0+31 of an activation row as split
 // BF16 in the core-matrix layout (four 16-byte stores per term).
-__device__ __forceinline__ void tc_store_act(TcSmem& S, int m, int c0, const float (&h)[32]) {
+__device__ __forceinline__ void tc_store_act(TcSmem& S, int g, int m, int c0, const float (&h)[32]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_pack(h[8 * j + 2 * e], h[8 * j + 2 * e + 1], hi[e], lo[e]);
         const int idx = cm_index(m, c0 + 8 * j);
-        *reinterpret_cast<uint4*>(S.Ah + idx) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(S.Al + idx) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<uint4*>(S.Ah[g] + idx) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(S.Al[g] + idx) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
 // Hidden layer epilogue: bias, GELU and the split A operand of the next layer
 // for the thread's sample and its 32 columns.
-__device__ __forceinline__ void tc_hidden_epilogue(TcSmem& S, uint32_t tcol, int m, int c0, const float* b) {
+__device__ __forceinline__ void tc_hidden_epilogue(TcSmem& S, int g, uint32_t tcol, int m, int c0, const float* b) {
     float h[32];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -648,16 +665,19 @@ __device__ __forceinline__ void tc_hidden_epilogue(TcSmem& S, uint32_t tcol, int
             h[16 * half + i] = gelu_fast(v[i] + b[c0 + 16 * half + i]);
         }
     }
-    tc_store_act(S, m, c0, h);
+    tc_store_act(S, g, m, c0, h);
 }
 
-__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs a) {
+__global__ void __launch_bounds__(kTcWarps * 32, 2) k_mlp_infer_tc(const InferArgs a) {
     extern __shared__ __align__(16) unsigned char smtc[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smtc);
     BlockTables& T = *reinterpret_cast<BlockTables*>(smtc + sizeof(TcSmem));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = 32 * (warp & 3) + lane;  // the thread's sample row (TMEM lane)
-    const int c0 = 32 * (warp >> 2);       // its 32 columns of a hidden layer
+    const int g = warp >> 3;                // the thread's group
+    const int m = 32 * (warp & 3) + lane;   // its sample row (TMEM lane)
+    const int hh = (warp >> 2) & 1;         // its half of a layer's columns
+    const int c0 = 32 * hh;
+    const bool issuer = (tid & 255) == 0;
     load_weights_tc(S, a.params, a.no);
     long long total = a.n;
     if (!a.kv) {
@@ -670,7 +690,7 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs 
         total = a.base[a.z1] - first;
     }
     if (tid == 0) {
-        mbar_init(&S.bar, 1);
+        for (int i = 0; i < kTcGroups; ++i) mbar_init(&S.bar[i], 1);
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -684,10 +704,12 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // the warp's lanes, column 0
+    const uint32_t dcol = tmem + (uint32_t)(64 * g);                 // the group's accumulator
+    const uint32_t tlane = dcol + ((uint32_t)(32 * (warp & 3)) << 16);  // the warp's lanes in it
     uint32_t phase = 0;
     const long long tiles = (total + kTcRows - 1) / kTcRows;
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * kTcGroups + g; tile < tiles;
+         tile += (long long)gridDim.x * kTcGroups) {
         const long long r = tile * kTcRows + m;
         float x = 0.f;
         if (r < total) {
@@ -700,17 +722,17 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs 
             for (int i = 0; i < 32; ++i) {
                 h[i] = gelu_fast(S.W1[c0 + i] * x + S.b1[c0 + i]);
             }
-            tc_store_act(S, m, c0, h);
+            tc_store_act(S, g, m, c0, h);
         }
-        if (!tc_run(S, tid, tmem, S.W2h, S.W2l, kH, phase++)) break;
-        tc_hidden_epilogue(S, tlane + (uint32_t)c0, m, c0, S.b2);
-        if (!tc_run(S, tid, tmem, S.W3h, S.W3l, kH, phase++)) break;
-        tc_hidden_epilogue(S, tlane + (uint32_t)c0, m, c0, S.b3);
-        if (!tc_run(S, tid, tmem, S.W4h, S.W4l, kMlpMaxOut, phase++)) break;
+        if (!tc_run(S, g, issuer, dcol, S.W2h, S.W2l, kH, phase++)) break;
+        tc_hidden_epilogue(S, g, tlane + (uint32_t)c0, m, c0, S.b2);
+        if (!tc_run(S, g, issuer, dcol, S.W3h, S.W3l, kH, phase++)) break;
+        tc_hidden_epilogue(S, g, tlane + (uint32_t)c0, m, c0, S.b3);
+        if (!tc_run(S, g, issuer, dcol, S.W4h, S.W4l, kMlpMaxOut, phase++)) break;
         {
-            // output columns 16 (warp div 4) .. +15: taps 8 (warp div 4) .. +7
+            // output columns 16 hh .. +15: taps 8 hh .. +7
             float v[16];
-            const int o0 = 16 * (warp >> 2);
+            const int o0 = 16 * hh;
             tc_ld16(tlane + (uint32_t)o0, v);
             if (r < total) {
 #pragma unroll
@@ -734,7 +756,9 @@ __global__ void __launch_bounds__(kTcWarps * 32) k_mlp_infer_tc(const InferArgs 
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols) : "memory");
     }
-    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(&S.bar)) : "memory");
+    if (tid == 0)
+        for (int i = 0; i < kTcGroups; ++i)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(&S.bar[i])) : "memory");
 }
 
 static int sm_count() {
@@ -745,12 +769,12 @@ static int sm_count() {
 }
 
 static cudaError_t launch_infer(const InferArgs& a, long long max_total, cudaStream_t s) {
-    // tcgen05 form: two CTAs of 128 samples per SM (73 KB of shared memory
-    // and 64 TMEM columns each)
+    // tcgen05 form: two CTAs per SM, each two groups of 128 samples per tile
+    // (105 KB of shared memory and 128 TMEM columns per CTA)
     const size_t smem = sizeof(TcSmem) + (a.kv ? 0 : block_tables_bytes(a.nw));
     cudaError_t e = ensure_smem(k_mlp_infer_tc, smem);
     if (e != cudaSuccess) return e;
-    long long grid = (max_total + kTcRows - 1) / kTcRows;
+    long long grid = (max_total + kTcGroups * kTcRows - 1) / (kTcGroups * kTcRows);
     const long long cap = (long long)sm_count() * 2;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
