@@ -332,7 +332,6 @@ static int fill_args(const fxmig_line* lines, int n, const fxmig_batch_plan& pla
         a.partials = lines[i].partials;
         a.status = reinterpret_cast<int*>(wsb);
         a.W = lp[i].W; a.C = C; a.G = lp[i].G; a.lines = lp[i].lines;
-        a.cwarps = kBatchWarps; a.ewarps = 0;
         a.img = lp[i].img;
         a.tma_ok = ((d.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(lines[i].vel) & 15) == 0);
         if (slabs) {  // autotuner: scratch wavefield and partial rows, first rows

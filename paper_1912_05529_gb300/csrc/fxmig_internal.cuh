@@ -188,8 +188,6 @@ struct MigratePlan {
     int cluster;   // persistent: CTAs per frequency group along x
     int groups;    // persistent: frequency groups; per-depth: frequency tiles
     int warps;     // warps per CTA
-    int cwarps;    // persistent: interior compute warps
-    int ewarps;    // persistent: edge warps (clusters only)
     int W;         // persistent: x segment per CTA (multiple of 8)
     int lines;     // persistent: max lines per group
     size_t smem;   // dynamic shared memory bytes per CTA

@@ -238,8 +238,6 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
             p->smem = smem;
             p->img = img ? 1 : 0;
             p->warps = cw;
-            p->cwarps = cw;
-            p->ewarps = 0;
             p->nparts = G;
         }
     }
@@ -315,7 +313,6 @@ cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* s
     a.partials = partials;
     a.status = status;
     a.W = plan.W; a.C = plan.cluster; a.G = plan.groups; a.lines = plan.lines;
-    a.cwarps = plan.cwarps; a.ewarps = plan.ewarps;
     a.img = plan.mode == FXMIG_MODE_PERSISTENT ? plan.img : 0;
     a.tma_ok = ((d->nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(use_slow ? (const float*)slow : vel) & 15) == 0);
     if (plan.precision != FXMIG_PREC_FP32) return launch_persistent_rp(plan, a, s);

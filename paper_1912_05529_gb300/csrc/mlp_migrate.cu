@@ -337,7 +337,6 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
         pa.partials = partials;
         pa.status = w.status;
         pa.W = plan.pplan.W; pa.C = plan.pplan.cluster; pa.G = plan.pplan.groups; pa.lines = plan.pplan.lines;
-        pa.cwarps = plan.pplan.cwarps;
         pa.img = plan.pplan.img;
         pa.tma_ok = 1;  // nx % 4 == 0 and the workspace arrays are 256-byte aligned
         pa.pair_cnt = w.cnt;

@@ -9,7 +9,8 @@
 //   - sums Re P over its lines into its partial image row (deterministic),
 //   - looks up the operator of every output point (fp32 index, Sec. III),
 //   - applies Eq. 1 with symmetric-pair packed f32x2 FMAs,
-//   - pushes the L edge outputs into its neighbours' halos (st.async, DSMEM),
+//   - sends each line's L edge outputs into its neighbours' halos (DSMEM:
+//     one bulk copy per strip, st.async around it),
 // and one CTA barrier replaces the paper's kernel exit (Sec. III, V).  The
 // slowness (or velocity) row of a later depth is staged by a 1-D TMA bulk
 // copy while the current depth is computed.
@@ -32,7 +33,6 @@ struct MigrateArgs {
     float* partials;        // [G][nz][nx]
     int* status;
     int W, C, G, lines, tma_ok;
-    int cwarps, ewarps;     // persistent: interior compute warps, edge warps
     int img;                // persistent: imaging buffer in shared memory (persistent_layout)
     // operators per (frequency, distinct slowness) pair instead of the table
     // (kPairs): `slow` holds every point's pair index within its row, `taps`

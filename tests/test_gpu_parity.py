@@ -199,3 +199,21 @@ def test_halo_strips(fx, L, prec):
     tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if prec == "FP32" else (1e-2, 1e-2)
     assert rel_l2(slabs[-1], P_ref) < tol_s
     assert rel_l2(image, img_ref) < tol_i
+
+
+def test_halo_strips_straddling_warps(fx):
+    # 496 traces over clusters of 2: segments of 31 chunks, so the items of
+    # line 1 start at lane 31 of a warp and its left strip (chunks 0-1)
+    # straddles two warps: that strip goes one output at a time while the
+    # other strips go whole
+    w = small_layered(nx=496, nz=20, L=12, seed=13, name="layered_496")
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    d = desc_of(fx, w, pr["k_max"])
+    launch = fx.Launch(mode=1, cluster=2, groups=max(1, w.nw // 3))
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch)
+    P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    assert rel_l2(slabs[-1], P_ref) < TOL_SLICE
+    assert rel_l2(image, img_ref) < TOL_IMAGE
