@@ -246,7 +246,11 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
 
 template <int LT>
 static cudaError_t launch_lt(const MigratePlan& plan, MigrateArgs a, cudaStream_t s, float2* ws_slab) {
-    if (plan.mode == FXMIG_MODE_PERSISTENT) return launch_persistent<LT, WsF32, TapF32>(plan, a, s);
+    if (plan.mode == FXMIG_MODE_PERSISTENT) {
+        if (halo_bulk_only<LT>(plan.W, plan.cluster, plan.lines, 8))
+            return launch_persistent<LT, WsF32, TapF32, false, true>(plan, a, s);
+        return launch_persistent<LT, WsF32, TapF32>(plan, a, s);
+    }
     auto kern = k_migrate_step<LT>;
     cudaError_t e = ensure_smem(kern, plan.smem);
     if (e != cudaSuccess) return e;

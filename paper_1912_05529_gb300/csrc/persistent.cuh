@@ -283,6 +283,32 @@ struct HaloStrips {
     static constexpr int kRightN = (LT - 1) + 2 * ((LT - 1) >> 3) + 1;
 };
 
+// Whether line s's left (right) strip goes whole: its chunks c < E
+// (c >= NC - E) are items of one 32-item block, i.e. of one warp's round.
+// With NC a multiple of 32 (the spread item mapping) they always are.
+__host__ __device__ inline bool strip_whole_left(int s, int NC, int E) {
+    return (NC & 31) == 0 || ((s * NC) & 31) + E <= 32;
+}
+__host__ __device__ inline bool strip_whole_right(int s, int NC, int E) {
+    return (NC & 31) == 0 || ((s * NC + NC - 1) & 31) + 1 >= E;
+}
+// Halos of a launch arrive entirely by bulk copies (FP32 values, strips of
+// an even number of slots at even slots, every line's strips whole): their
+// bytes are written by the async proxy and complete on the receiving CTA's
+// mbarrier, so a CTA-scope acquire on that barrier suffices (as for any
+// bulk copy into a CTA's shared memory).  Otherwise st.async bytes, whose
+// complete_tx releases at cluster scope, need a cluster-scope acquire.
+template <int LT>
+inline bool halo_bulk_only(int W, int C, int lines, int esize) {
+    typedef HaloStrips<LT> HS;
+    if (C <= 1 || esize != 8 || (W & 7) != 0) return false;
+    if (HS::kLeft0 % 2 != 0 || HS::kLeftN % 2 != 0 || HS::kRightN % 2 != 0) return false;
+    const int NC = W >> 3, E = (LT + 7) >> 3 < NC ? (LT + 7) >> 3 : NC;
+    for (int s = 0; s < lines; ++s)
+        if (!strip_whole_left(s, NC, E) || !strip_whole_right(s, NC, E)) return false;
+    return true;
+}
+
 // Send slots [0, n) of a strip from this CTA's shared memory (src) to the
 // neighbour's (dst, shared::cluster), counted on the neighbour's mbarrier.
 // src and dst have the same address modulo 16 bytes: the 16-byte aligned
@@ -309,7 +335,9 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 // partial image `part`, added to what it holds when `accumulate` is set.  On return every mbarrier used
 // is invalidated and no copy or remote store is in flight, so the memory can
 // hold the next group.
-template <int LT, class WS, class TP, bool kPairs = false>
+// kCtaHalo: the launch's halos arrive by bulk copies only (halo_bulk_only),
+// so the halo waits acquire at CTA scope.
+template <int LT, class WS, class TP, bool kPairs = false, bool kCtaHalo = false>
 __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned char* smem, int part,
                                           bool accumulate) {
     typedef typename WS::T T;
@@ -499,8 +527,8 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     // always with the spread mapping below, else unless the line's items
     // cross a block boundary there.  Bytes each halo barrier phase receives:
     // per line the neighbour's strip (pads included) or its LT outputs.
-    auto left_whole = [&](int s) { return strips && (spread || (((s * NC) & 31) + E <= 32)); };
-    auto right_whole = [&](int s) { return strips && (spread || (((s * NC + NC - 1) & 31) + 1 >= E)); };
+    auto left_whole = [&](int s) { return strips && strip_whole_left(s, NC, E); };
+    auto right_whole = [&](int s) { return strips && strip_whole_right(s, NC, E); };
     uint32_t halo_bytes_l = 0, halo_bytes_r = 0;
     for (int s = 0; s < mg; ++s) {
         halo_bytes_l += right_whole(s) ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB;
@@ -591,8 +619,13 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 // the neighbours' outputs of step z-1 have landed in cur's halo
                 const bool wl = __any_sync(0xffffffffu, need_l), wr = __any_sync(0xffffffffu, need_r);
                 bool ok = true;
-                if (wl) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
-                if (wr) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                if constexpr (kCtaHalo) {
+                    if (wl) ok &= mbar_wait_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                    if (wr) ok &= mbar_wait_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                } else {
+                    if (wl) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                    if (wr) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                }
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             uint32_t mask = 0;
@@ -649,18 +682,18 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
 
 // One launch of the persistent form: cluster blockIdx.x / C runs group
 // blockIdx.x / C of the problem.
-template <int LT, class WS, class TP, bool kPairs = false>
+template <int LT, class WS, class TP, bool kPairs = false, bool kCtaHalo = false>
 __global__ void __launch_bounds__(kPersistentMaxThreads, 1) k_migrate_persistent(const MigrateArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int g = (int)(blockIdx.x / a.C);
-    run_group<LT, WS, TP, kPairs>(a, g, smem, g, false);
+    run_group<LT, WS, TP, kPairs, kCtaHalo>(a, g, smem, g, false);
 }
 
 
 // One launch of the persistent form for compiled LT and storage policies.
-template <int LT, class WS, class TP, bool kPairs = false>
+template <int LT, class WS, class TP, bool kPairs = false, bool kCtaHalo = false>
 cudaError_t launch_persistent(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
-    auto kern = k_migrate_persistent<LT, WS, TP, kPairs>;
+    auto kern = k_migrate_persistent<LT, WS, TP, kPairs, kCtaHalo>;
     cudaError_t e = ensure_smem(kern, plan.smem, plan.cluster > 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
