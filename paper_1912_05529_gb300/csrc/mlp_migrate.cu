@@ -297,6 +297,15 @@ static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& 
     return cudaSuccess;
 }
 
+// One pair-mode persistent launch, with CTA-scope halo waits when the
+// halos arrive by bulk copies only (halo_bulk_only).
+template <int LT>
+static cudaError_t launch_pairs(const MigratePlan& pp, const MigrateArgs& pa, cudaStream_t s) {
+    if (halo_bulk_only<LT>(pp.W, pp.cluster, pp.lines, 8))
+        return launch_persistent<LT, WsF32, TapF32, true, true>(pp, pa, s);
+    return launch_persistent<LT, WsF32, TapF32, true>(pp, pa, s);
+}
+
 cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, void* slab, const float* vel,
                                const float* params, float* partials, int z_begin, int z_end, void* ws,
                                cudaStream_t s) {
@@ -351,10 +360,10 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
             pa.z_end = z1;
             pa.pair_z0 = z0;
             switch (plan.LT) {
-                case 4: e = launch_persistent<4, WsF32, TapF32, true>(plan.pplan, pa, s); break;
-                case 8: e = launch_persistent<8, WsF32, TapF32, true>(plan.pplan, pa, s); break;
-                case 12: e = launch_persistent<12, WsF32, TapF32, true>(plan.pplan, pa, s); break;
-                case 16: e = launch_persistent<16, WsF32, TapF32, true>(plan.pplan, pa, s); break;
+                case 4: e = launch_pairs<4>(plan.pplan, pa, s); break;
+                case 8: e = launch_pairs<8>(plan.pplan, pa, s); break;
+                case 12: e = launch_pairs<12>(plan.pplan, pa, s); break;
+                case 16: e = launch_pairs<16>(plan.pplan, pa, s); break;
                 default: e = cudaErrorInvalidValue; break;
             }
             if (e != cudaSuccess) return e;
