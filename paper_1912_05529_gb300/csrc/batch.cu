@@ -24,7 +24,13 @@
 
 namespace fxmig_impl {
 
-constexpr int kBatchWarps = 12;
+// 12 warps: with clusters of 2 or more CTAs, 11 compute warps and the edge
+// warp of the depth loop (run_group); clusters of 1 compute with all 12.
+// Twelve warps keep 168 registers per thread (three warps per SM
+// sub-partition), which the batch kernel's switch over the compiled
+// half-lengths needs more than a thirteenth warp (measured on the 64-line
+// batch: 530 ms against 570 ms).
+constexpr int kBatchWarps = kPersistentMaxWarps;
 
 struct BatchLineArgs {
     MigrateArgs a;

@@ -288,4 +288,47 @@ __device__ __forceinline__ u64 fir1(const typename WS::T* __restrict__ line, int
     return f2_pack(av.x - bv.y, av.y + bv.x);
 }
 
+// Eq. 1 for the two outputs x and x + 1 (x even) of a line, each with its
+// own operator (taps tp0 and tp1), in the summation order of fir1 and fir8
+// (n = 0, then the pairs n = 1..LT ascending).  The window x-LT..x+1+LT is
+// addressed from the 8-aligned block of x as in fir1.  re0 / re1: real parts
+// of the input values at x and x + 1.
+template <int LT, class WS, class TP>
+__device__ __forceinline__ void fir2(const typename WS::T* __restrict__ line, int x,
+                                     const typename TP::E* __restrict__ tp0, const typename TP::E* __restrict__ tp1,
+                                     u64& o0, u64& o1, float& re0, float& re1) {
+    const int a = x & 7;
+    const typename WS::T* bp = line + 10 * (x >> 3) + a;
+    int adj[8];
+    adj[0] = 0;
+#pragma unroll
+    for (int m = 1; m < 8; ++m) adj[m] = (a >= 8 - m) ? 2 : 0;
+    u64 w[2 * LT + 2];
+#pragma unroll
+    for (int d = 0; d < 2 * LT + 2; ++d) w[d] = WS::ld1(bp + adj[d & 7] + d + 2 * (d >> 3));
+    re0 = f2_unpack(w[LT]).x;
+    re1 = f2_unpack(w[LT + 1]).x;
+    u64 hr, hi;
+    TP::ld(tp0, hr, hi);
+    u64 A0 = f2_mul(hr, w[LT]), B0 = f2_mul(hi, w[LT]);
+    TP::ld(tp1, hr, hi);
+    u64 A1 = f2_mul(hr, w[LT + 1]), B1 = f2_mul(hi, w[LT + 1]);
+#pragma unroll
+    for (int n = 1; n <= LT; ++n) {
+        TP::ld(tp0 + n, hr, hi);
+        const u64 t0 = f2_add(w[LT - n], w[LT + n]);
+        A0 = f2_fma(hr, t0, A0);
+        B0 = f2_fma(hi, t0, B0);
+        TP::ld(tp1 + n, hr, hi);
+        const u64 t1 = f2_add(w[LT + 1 - n], w[LT + 1 + n]);
+        A1 = f2_fma(hr, t1, A1);
+        B1 = f2_fma(hi, t1, B1);
+    }
+    float2 av = f2_unpack(A0), bv = f2_unpack(B0);
+    o0 = f2_pack(av.x - bv.y, av.y + bv.x);
+    av = f2_unpack(A1);
+    bv = f2_unpack(B1);
+    o1 = f2_pack(av.x - bv.y, av.y + bv.x);
+}
+
 }  // namespace fxmig_impl

@@ -178,7 +178,7 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
     const int smax = device_smem_optin();
     const int req_c = (launch && launch->cluster > 0) ? launch->cluster : 0;
     if (req_c && req_c != 1 && req_c != 2 && req_c != 4 && req_c != 8) return FXMIG_EINVAL;
-    const int max_warps = kPersistentMaxThreads / 32;
+    const int max_warps = kPersistentMaxWarps;  // compute warps (the edge warp is added at launch)
     if (launch && launch->warps > 0 && (launch->warps > max_warps || launch->warps < 1)) return FXMIG_EINVAL;
     double best = 1e300;
     bool found = false;

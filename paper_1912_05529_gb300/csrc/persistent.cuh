@@ -8,9 +8,11 @@
 // steps.  Per depth step each CTA
 //   - sums Re P over its lines into its partial image row (deterministic),
 //   - looks up the operator of every output point (fp32 index, Sec. III),
-//   - applies Eq. 1 with symmetric-pair packed f32x2 FMAs,
-//   - sends each line's L edge outputs into its neighbours' halos (DSMEM:
-//     one bulk copy per strip, st.async around it),
+//   - applies Eq. 1 with symmetric-pair packed f32x2 FMAs: the compute warps
+//     take the interior of the segment as 8-output items and never wait on
+//     a neighbour; one edge warp waits for the halos, computes the outputs
+//     near the segment edges and sends each line's L edge outputs into its
+//     neighbours' halos (DSMEM: one bulk copy per strip, st.async around it),
 // and one CTA barrier replaces the paper's kernel exit (Sec. III, V).  The
 // slowness (or velocity) row of a later depth is staged by a 1-D TMA bulk
 // copy while the current depth is computed.
@@ -68,7 +70,13 @@ __host__ __device__ inline PersistentSmem persistent_layout(int W, int lines, in
 }
 
 // ------------------------------------------------------------ persistent form
-constexpr int kPersistentMaxThreads = 384;  // up to 12 warps: 168 registers per thread
+// Outputs per lane of the edge warp: two outputs that share one window, each
+// with its own operator (fir2).
+constexpr int kEdgeOut = 2;
+// Up to 12 compute warps, plus one edge warp when the CTA has cluster
+// neighbours: 13 warps, 152 registers per thread.
+constexpr int kPersistentMaxWarps = 12;
+constexpr int kPersistentMaxThreads = (kPersistentMaxWarps + 1) * 32;
 
 // Per-CTA constants of the persistent kernel.
 struct SegCtx {
@@ -174,33 +182,6 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, c
     return skip;
 }
 
-// Number the set bits of each lane's mask across the warp: returns the
-// warp total; excl receives the bits of the lanes below.
-__device__ __forceinline__ uint32_t warp_enumerate(uint32_t mask, int lane, uint32_t& excl) {
-    const uint32_t cnt = __popc(mask);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    excl = incl - cnt;
-    return __shfl_sync(0xffffffffu, incl, 31);
-}
-
-// The lane that owns bit number it of the warp's enumeration (excl from
-// warp_enumerate), found by a binary search over the lanes' prefix counts.
-__device__ __forceinline__ int warp_owner(uint32_t excl, uint32_t it) {
-    int owner = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int cand = owner + step;
-        const uint32_t ex = __shfl_sync(0xffffffffu, excl, cand);
-        if (ex <= it) owner = cand;
-    }
-    return owner;
-}
-
 // Warp-cooperative recomputation of the outputs flagged in each lane's
 // `mask` (line s, chunk at xl0; bit 0 is never set): the flagged outputs of
 // the whole warp are numbered by output position r, then by lane, from one
@@ -244,32 +225,6 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
     }
 }
 
-// Warp-cooperative halo push of the round's edge outputs: bit r of a lane's
-// `mask` marks output xl0 + r of line s, which lies within LT of a segment
-// edge that has a neighbour.  The outputs are numbered across the warp and
-// sent one per lane from the next buffer (written by this warp's main items
-// and fixups before the __syncwarp that precedes the call), so the remote
-// stores of a round go out as a few warp-wide st.async.  All 32 lanes must
-// call.
-template <int LT, class WS>
-__device__ __forceinline__ void coop_push(const SegCtx& g, uint32_t mask, int s, int xl0,
-                                          const typename WS::T* nxt, size_t nxt_off, int lane, int pb) {
-    uint32_t excl;
-    const uint32_t total = warp_enumerate(mask, lane, excl);
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t it = base + lane;
-        const int owner = warp_owner(excl, it);
-        const uint32_t ex_o = __shfl_sync(0xffffffffu, excl, owner);
-        const uint32_t mask_o = __shfl_sync(0xffffffffu, mask, owner);
-        const int s_o = __shfl_sync(0xffffffffu, s, owner);
-        const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
-        if (it < total) {
-            const int x = x0_o + (int)__fns(mask_o, 0, (int)(it - ex_o) + 1);
-            push_halo<LT, WS>(g, nxt_off, s_o, x, WS::ld1(nxt + (size_t)s_o * g.SP + phys(x + LT)), pb);
-        }
-    }
-}
-
 // Halo strips of one line in the padded layout, pads included.  The left
 // strip holds outputs x in [0, LT) at slots [phys(LT), phys(2LT-1)] and
 // lands phys(W) slots further on in the left neighbour's right halo; the
@@ -283,30 +238,26 @@ struct HaloStrips {
     static constexpr int kRightN = (LT - 1) + 2 * ((LT - 1) >> 3) + 1;
 };
 
-// Whether line s's left (right) strip goes whole: its chunks c < E
-// (c >= NC - E) are items of one 32-item block, i.e. of one warp's round.
-// With NC a multiple of 32 (the spread item mapping) they always are.
-__host__ __device__ inline bool strip_whole_left(int s, int NC, int E) {
-    return (NC & 31) == 0 || ((s * NC) & 31) + E <= 32;
+// Whether the halos go as whole strips (one per line and side, sent by the
+// edge warp once the line's edge outputs are in shared memory): segments of
+// whole 8-output chunks whose padded line length keeps a strip and its
+// landing place at the same 16-byte alignment.  Otherwise every halo output
+// goes by its own st.async.
+__host__ __device__ inline bool halo_strips(int W, int C, int esize) {
+    return C > 1 && (W & 7) == 0 && ((W + 2 * (W >> 3)) * esize) % 16 == 0;
 }
-__host__ __device__ inline bool strip_whole_right(int s, int NC, int E) {
-    return (NC & 31) == 0 || ((s * NC + NC - 1) & 31) + 1 >= E;
-}
-// Halos of a launch arrive entirely by bulk copies (FP32 values, strips of
-// an even number of slots at even slots, every line's strips whole): their
-// bytes are written by the async proxy and complete on the receiving CTA's
-// mbarrier, so a CTA-scope acquire on that barrier suffices (as for any
-// bulk copy into a CTA's shared memory).  Otherwise st.async bytes, whose
-// complete_tx releases at cluster scope, need a cluster-scope acquire.
+// Halos of a launch arrive entirely by bulk copies (FP32 values, whole
+// strips of an even number of slots at even slots): their bytes are written
+// by the async proxy and complete on the receiving CTA's mbarrier, so a
+// CTA-scope acquire on that barrier suffices (as for any bulk copy into a
+// CTA's shared memory).  Otherwise st.async bytes, whose complete_tx
+// releases at cluster scope, need a cluster-scope acquire.
 template <int LT>
 inline bool halo_bulk_only(int W, int C, int lines, int esize) {
     typedef HaloStrips<LT> HS;
-    if (C <= 1 || esize != 8 || (W & 7) != 0) return false;
-    if (HS::kLeft0 % 2 != 0 || HS::kLeftN % 2 != 0 || HS::kRightN % 2 != 0) return false;
-    const int NC = W >> 3, E = (LT + 7) >> 3 < NC ? (LT + 7) >> 3 : NC;
-    for (int s = 0; s < lines; ++s)
-        if (!strip_whole_left(s, NC, E) || !strip_whole_right(s, NC, E)) return false;
-    return true;
+    (void)lines;
+    if (esize != 8 || !halo_strips(W, C, esize)) return false;
+    return HS::kLeft0 % 2 == 0 && HS::kLeftN % 2 == 0 && HS::kRightN % 2 == 0;
 }
 
 // Send slots [0, n) of a strip from this CTA's shared memory (src) to the
@@ -493,28 +444,45 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         sc.bar_left[b] = sc.has_left ? map_cluster_rank(&hbar[2 + b], rank - 1) : 0u;   // its right halo
         sc.bar_right[b] = sc.has_right ? map_cluster_rank(&hbar[b], rank + 1) : 0u;     // its left halo
     }
-    // Halo pushes: one strip per line and side, sent whole by the warp that
-    // owns the strip's chunks when they fall in one warp's round and a strip
-    // and its landing place have the same 16-byte alignment; else one
-    // st.async per output (bytes per barrier phase below).
+    // Warps.  With cluster neighbours (C > 1) the last warp is the edge warp:
+    // it alone reads the halos and computes the outputs within E chunks of a
+    // segment edge that has a neighbour (the "edge" chunks), two outputs per
+    // lane, each with its own operator, and sends them to the neighbours'
+    // halos as soon as they are in shared memory.  The other (compute) warps
+    // take every other chunk as 8-output items and never wait on a halo, so
+    // the halo exchange is one short item plus the DSMEM latency per step,
+    // off the compute warps' path.
+    const bool edges = C > 1;
+    const int ncw = edges ? nwarps - 1 : nwarps;  // compute warps
+    const bool edge_warp = edges && warp == nwarps - 1;
+    // The thread that stages the velocity rows, arms the halo barriers and
+    // waits for each staged row: lane 0 of the edge warp, which has that
+    // time while it waits for the halos (else thread 0).
+    const bool duty = edges ? (edge_warp && lane == 0) : tid == 0;
+    // Halo strips: one per line and side with a neighbour, sent whole by the
+    // edge warp (pads included; the 16-byte aligned middle as a bulk copy,
+    // the slots around it by st.async), or one st.async per output when the
+    // padded line length breaks the strip alignment (halo_strips).
     typedef HaloStrips<LT> HS;
     const int physW = W + 2 * (W >> 3);
-    const bool strips = C > 1 && (W & 7) == 0 && (physW * WS::kBytes) % 16 == 0;
+    const bool strips = halo_strips(W, C, WS::kBytes);
     const uint32_t kB = (uint32_t)WS::kBytes;
 
-    // Work items: (line, 8-output chunk), one per lane and round.  Chunks
-    // within LT of a segment edge ("edge" chunks) read the halo, and their
-    // outputs go to the neighbours' halos.  Halo exchange is point to point:
-    // after each round of items the warp that owns a line's edge chunks sends
-    // the line's halo strip (see the halo pushes above), and a CTA waits on
-    // its own halo barrier of the step's parity before it reads its halo;
-    // neighbours can never be more
-    // than one step apart, so two parities suffice and no cluster-wide
-    // barrier is needed.  One CTA barrier ends a depth step; the image row of
-    // the step is summed right after it from the imaging buffer (overlapping
-    // the neighbours' halo transfers), or without that buffer just before it
-    // from the step's input wavefield.
-    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;  // edge chunks per side
+    // Edge chunks of a line: c < EL on the left and c >= NC - NR on the
+    // right (E = ceil(LT / 8) chunks per side, fewer on the right when the
+    // segment holds fewer than 2E chunks).  Only they read the halo (the
+    // window of chunk c spans outputs 8c - LT .. 8c + 7 + LT) and only they
+    // feed the neighbours' halos (outputs x < LT or x >= W - LT).  Halo
+    // exchange is point to point: a CTA waits on its own halo barrier of the
+    // step's parity before its edge warp reads the halo; neighbours can never
+    // be more than one step apart (the edge warp's wait precedes the step
+    // barrier), so two parities suffice and no cluster-wide barrier is
+    // needed.  One CTA barrier ends a depth step; the image row of the step
+    // is summed right after it from the imaging buffer, or without that
+    // buffer just before it from the step's input wavefield.
+    const int E = (C > 1) ? min((LT + 7) >> 3, NC) : 0;
+    const int EL = sc.has_left ? E : 0;
+    const int NR = sc.has_right ? min(E, NC - EL) : 0;
     const int n_items = mg * NC;
     // item / NC by a multiply-high with m = ceil(2^32 / NC): exact while
     // item * NC < 2^32, which n_items * NC < 2^32 guarantees; m fits 32 bits
@@ -522,19 +490,11 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
     const uint32_t nc_magic = (uint32_t)((0xffffffffull + (uint64_t)NC) / (uint64_t)NC);
     const bool magic_ok = NC >= 2 && (uint64_t)n_items * (uint64_t)NC < (1ull << 32);
     const bool spread = (NC & 31) == 0;  // lines of whole warps of items
-    // Line s's left (right) strip goes whole when its chunks c < E
-    // (c >= NC - E) are items of one 32-item block, i.e. of one warp's round:
-    // always with the spread mapping below, else unless the line's items
-    // cross a block boundary there.  Bytes each halo barrier phase receives:
-    // per line the neighbour's strip (pads included) or its LT outputs.
-    auto left_whole = [&](int s) { return strips && strip_whole_left(s, NC, E); };
-    auto right_whole = [&](int s) { return strips && strip_whole_right(s, NC, E); };
-    uint32_t halo_bytes_l = 0, halo_bytes_r = 0;
-    for (int s = 0; s < mg; ++s) {
-        halo_bytes_l += right_whole(s) ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB;
-        halo_bytes_r += left_whole(s) ? (uint32_t)HS::kLeftN * kB : (uint32_t)LT * kB;
-    }
-    // line s and chunk c of a valid item.  With `spread`, a warp's 32 items
+    // Bytes each halo barrier phase receives: per line the neighbour's strip
+    // (pads included) or its LT outputs.
+    const uint32_t halo_bytes_l = (uint32_t)mg * (strips ? (uint32_t)HS::kRightN * kB : (uint32_t)LT * kB);
+    const uint32_t halo_bytes_r = (uint32_t)mg * (strips ? (uint32_t)HS::kLeftN * kB : (uint32_t)LT * kB);
+    // line s and chunk c of a compute item.  With `spread`, a warp's 32 items
     // of a line, j = 32a + 8q + r, take chunk 8 (q NC/32 + a) + r, so each
     // warp covers four blocks of 8 chunks a quarter of the line apart
     // (velocity changes, which cost extra work, are shared between warps); a
@@ -544,40 +504,27 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         const int j = item - s * NC;
         c = spread ? ((((j >> 3) & 3) * (NC >> 5) + (j >> 5)) << 3) + (j & 7) : j;
     };
-    // A lane's item of a round: line s, first output xl0 and flags: bit 0
-    // work (the chunk starts inside the segment), bits 1 / 2 the chunk reads
-    // and feeds the left / right halo, bits 3 / 4 it starts the line's left
-    // strip / ends its right strip, bits 8-15 its outputs that go to a
-    // neighbour's halo one by one (st.async form).  The push flags hold for
-    // steps whose outputs feed a further step.  Chunks c < E read the left
-    // halo and push to the left neighbour, chunks c >= NC - E the right ones
-    // (both also when the chunk lies beyond the line end and only pushes
-    // zeros).  Waiting for the neighbour's previous step on that side is what
-    // keeps the two CTAs within one step of each other, so a pusher waits
-    // even when it reads nothing.
-    auto item_state = [&](int item, int& s, int& xl0, uint32_t& f) {
+    // A compute lane's item of a round: line s, first output xl0, and whether
+    // it has work (an interior chunk that starts inside the segment; edge
+    // chunks belong to the edge warp).
+    auto item_state = [&](int item, int& s, int& xl0, bool& work) {
         s = 0;
         xl0 = 0;
-        f = 0;
+        work = false;
         if (item >= n_items) return;
         int c;
         item_chunk(item, s, c);
         xl0 = c << 3;
-        const bool need_l = sc.has_left && c < E, need_r = sc.has_right && c >= NC - E;
-        f = (xl0 < wv ? 1u : 0u) | (need_l ? 2u : 0u) | (need_r ? 4u : 0u);
-        const bool lw = left_whole(s), rw = right_whole(s);
-        f |= (need_l && lw && c == 0) ? 8u : 0u;
-        f |= (need_r && rw && c == NC - 1) ? 16u : 0u;
-        if ((need_l && !lw) || (need_r && !rw)) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-                if ((need_l && !lw && xl0 + r < LT) || (need_r && !rw && xl0 + r >= W - LT)) f |= 256u << r;
-        }
+        work = xl0 < wv && c >= EL && c < NC - NR;
     };
     // the first round's item is the same at every step
     int s_first, xl0_first;
-    uint32_t f_first;
-    item_state(warp * 32 + lane, s_first, xl0_first, f_first);
+    bool work_first;
+    item_state(warp * 32 + lane, s_first, xl0_first, work_first);
+    // The edge warp's lanes: kEdgeOut outputs each, the edge chunks of a
+    // line on consecutive lanes, in rounds of 32.
+    const int e_per_line = 8 * (EL + NR) / kEdgeOut;  // edge lane units per line
+    const int e_units = mg * e_per_line;
 
     for (int z = a.z_begin; z < a.z_end; ++z) {
         const int zb = (z - a.z_begin) & 1;
@@ -593,7 +540,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         const int pb = (z + 1) & 1;                         // receivers' barrier parity
         const bool halo_wait = (C > 1) && (z > a.z_begin);
         const uint32_t hpar = (uint32_t)(((z - a.z_begin - 1) >> 1) & 1);
-        if (tid == 0) {
+        if (duty) {
             // row z+kRowAhead goes to the slot of row z-1, which nobody reads now
             if (z + kRowAhead < a.z_end) issue_row(z + kRowAhead);
             if (halo_wait) {
@@ -602,53 +549,83 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
             }
         }
 
-        for (int base = warp * 32; base < n_items; base += nwarps * 32) {
-            int s, xl0;
-            uint32_t f;
-            if (base == warp * 32) {
-                s = s_first;
-                xl0 = xl0_first;
-                f = f_first;
-            } else {
-                item_state(base + lane, s, xl0, f);
-            }
-            const bool work = f & 1u, need_l = f & 2u, need_r = f & 4u;
-            const bool issue_l = push && (f & 8u), issue_r = push && (f & 16u);
-            const uint32_t pmask = push ? (f >> 8) & 0xffu : 0u;
+        if (edge_warp) {
             if (halo_wait) {
                 // the neighbours' outputs of step z-1 have landed in cur's halo
-                const bool wl = __any_sync(0xffffffffu, need_l), wr = __any_sync(0xffffffffu, need_r);
                 bool ok = true;
                 if constexpr (kCtaHalo) {
-                    if (wl) ok &= mbar_wait_bounded(&hbar[z & 1], hpar, kHaloPolls);
-                    if (wr) ok &= mbar_wait_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                    if (sc.has_left) ok &= mbar_wait_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                    if (sc.has_right) ok &= mbar_wait_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
                 } else {
-                    if (wl) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
-                    if (wr) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
+                    if (sc.has_left) ok &= mbar_wait_cluster_bounded(&hbar[z & 1], hpar, kHaloPolls);
+                    if (sc.has_right) ok &= mbar_wait_cluster_bounded(&hbar[2 + (z & 1)], hpar, kHaloPolls);
                 }
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
-            uint32_t mask = 0;
-            int idx1 = -1;
-            if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps, idx1);
-            if (__any_sync(0xffffffffu, mask != 0u))
-                coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, idx1, cur, nxt, srow, qz, taps, lane);
-            if (__any_sync(0xffffffffu, issue_l || issue_r)) {
-                // the strips' outputs (main items, fixups of this warp) are in
-                // nxt; make them visible to the copy engine, then send
+            for (int u0 = 0; u0 < e_units; u0 += 32) {
+                const int u = u0 + lane;
+                if (u < e_units) {
+                    const int s = u / e_per_line;
+                    const int rem = u - s * e_per_line;
+                    const int k = rem / (8 / kEdgeOut);
+                    const int c = k < EL ? k : NC - NR + (k - EL);
+                    const int x = 8 * c + kEdgeOut * (rem & (8 / kEdgeOut - 1));
+                    const float q = qz[s];
+                    const T* cl = cur + (size_t)s * SP;
+                    T* dl = nxt + (size_t)s * SP;
+                    u64 o0 = 0ull, o1 = 0ull;
+                    float re0 = 0.f, re1 = 0.f;
+                    if (x < wv) {
+                        const int i0 = op_index<kPairs>(q, srow[x], a.nk);
+                        const int i1 = x + 1 < wv ? op_index<kPairs>(q, srow[x + 1], a.nk) : i0;
+                        fir2<LT, WS, TP>(cl, x, taps + (size_t)i0 * (LT + 1), taps + (size_t)i1 * (LT + 1), o0,
+                                         o1, re0, re1);
+                        if (x + 1 >= wv) o1 = 0ull;
+                    }
+                    WS::st1(dl + phys(x + LT), o0);
+                    WS::st1(dl + phys(x + 1 + LT), o1);
+                    if (imgz) *reinterpret_cast<float2*>(imgz + (size_t)s * W + x) = make_float2(re0, re1);
+                    if (push && !strips) {
+                        push_halo<LT, WS>(sc, nxt_off, s, x, o0, pb);
+                        push_halo<LT, WS>(sc, nxt_off, s, x + 1, o1, pb);
+                    }
+                }
+            }
+            if (push && strips) {
+                // the edge outputs are in nxt; make them visible to the copy
+                // engine, then send each strip whole, one (line, side) per
+                // lane.  Every side with a neighbour sends its strip (a
+                // segment of fewer than 2E chunks counts its chunks once, as
+                // left-edge chunks, but still feeds both sides).
                 fence_proxy_async_smem();
                 __syncwarp();
-                const uint32_t line = (uint32_t)(nxt_off + (size_t)s * SP);
-                if (issue_l)
-                    send_strip<WS>(sc.nb_left + (line + physW + HS::kLeft0) * kB, nxt + (size_t)s * SP + HS::kLeft0,
-                                   HS::kLeftN, pb ? sc.bar_left[1] : sc.bar_left[0]);
-                if (issue_r)
-                    send_strip<WS>(sc.nb_right + line * kB, nxt + (size_t)s * SP + physW, HS::kRightN,
-                                   pb ? sc.bar_right[1] : sc.bar_right[0]);
+                for (int j = lane; j < 2 * mg; j += 32) {
+                    const int s = j >> 1;
+                    const uint32_t line = (uint32_t)(nxt_off + (size_t)s * SP);
+                    if ((j & 1) == 0 && sc.has_left)
+                        send_strip<WS>(sc.nb_left + (line + physW + HS::kLeft0) * kB, nxt + (size_t)s * SP + HS::kLeft0,
+                                       HS::kLeftN, pb ? sc.bar_left[1] : sc.bar_left[0]);
+                    if ((j & 1) == 1 && sc.has_right)
+                        send_strip<WS>(sc.nb_right + line * kB, nxt + (size_t)s * SP + physW, HS::kRightN,
+                                       pb ? sc.bar_right[1] : sc.bar_right[0]);
+                }
             }
-            if (__any_sync(0xffffffffu, pmask != 0u)) {
-                __syncwarp();  // the round's outputs (main items, fixups) are in nxt
-                coop_push<LT, WS>(sc, pmask, s, xl0, nxt, nxt_off, lane, pb);
+        } else {
+            for (int base = warp * 32; base < n_items; base += ncw * 32) {
+                int s, xl0;
+                bool work;
+                if (base == warp * 32) {
+                    s = s_first;
+                    xl0 = xl0_first;
+                    work = work_first;
+                } else {
+                    item_state(base + lane, s, xl0, work);
+                }
+                uint32_t mask = 0;
+                int idx1 = -1;
+                if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps, idx1);
+                if (__any_sync(0xffffffffu, mask != 0u))
+                    coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, idx1, cur, nxt, srow, qz, taps, lane);
             }
         }
         // velocity rows are converted by the whole CTA one step ahead
@@ -658,7 +635,7 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
         }
         {
             const int zw = a.slow ? z + 1 : z + 2;
-            if (tid == 0 && zw < a.z_end) wait_row(zw);
+            if (duty && zw < a.z_end) wait_row(zw);
         }
         if (!img) reduce_image_row(z, cur, tid, nthr);
         __syncthreads();
@@ -697,8 +674,11 @@ cudaError_t launch_persistent(const MigratePlan& plan, const MigrateArgs& a, cud
     cudaError_t e = ensure_smem(kern, plan.smem, plan.cluster > 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
+    // plan.warps compute warps, plus the edge warp when the CTAs of a
+    // cluster exchange halos
+    if (plan.warps < 1 || plan.warps > kPersistentMaxWarps) return cudaErrorInvalidValue;
     cfg.gridDim = dim3(plan.groups * plan.cluster);
-    cfg.blockDim = dim3(plan.warps * 32);
+    cfg.blockDim = dim3((plan.warps + (plan.cluster > 1 ? 1 : 0)) * 32);
     cfg.dynamicSmemBytes = plan.smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];

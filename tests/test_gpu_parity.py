@@ -202,10 +202,10 @@ def test_halo_strips(fx, L, prec):
 
 
 def test_halo_strips_straddling_warps(fx):
-    # 496 traces over clusters of 2: segments of 31 chunks, so the items of
-    # line 1 start at lane 31 of a warp and its left strip (chunks 0-1)
-    # straddles two warps: that strip goes one output at a time while the
-    # other strips go whole
+    # 496 traces over clusters of 2: segments of 31 chunks (not a multiple
+    # of 32, so the compute items of a line run across warp boundaries and
+    # the line's edge chunks fall at odd lanes); the edge warp still sends
+    # every strip whole
     w = small_layered(nx=496, nz=20, L=12, seed=13, name="layered_496")
     v, refl, sec = layered_inputs(w)
     pr = problem(w, v, sec)
