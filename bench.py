@@ -295,6 +295,42 @@ def measure_precision(fx, d, b, slab0, steps, flush, launch, prec):
     return {"ms_per_step": float(np.mean(ms)), "partials": nparts, "image": image.cpu().numpy()}
 
 
+def measure_per_depth(fx, d, b, slab0, steps, flush):
+    """The per-depth-launch form (one Eq. 1 launch per depth row, the wavefield
+    streaming through L2/HBM) on the same inputs: mean CUDA-event time of
+    fxmig_migrate_ex + fxmig_image, its image, and the migrate time alone for
+    the wavefield-traffic rate (16 bytes per point x frequency)."""
+    import torch
+    lc = fx.Launch(mode=fx.FXMIG_MODE_PER_DEPTH)
+    nparts = fx.fxmig_num_partials(d, lc)
+    partials = torch.zeros((nparts, d.nz, d.nx), dtype=torch.float32, device="cuda")
+    image = torch.empty((d.nz, d.nx), dtype=torch.float32, device="cuda")
+    slab = torch.empty_like(slab0)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        slab.copy_(slab0)
+        fx.fxmig_migrate_ex(d, lc, slab, b.vel, b.table, partials, 0, d.nz, b.ws_mig)
+        fx.fxmig_image(d, partials, image)
+    torch.cuda.synchronize()
+    if fx.fxmig_check(b.ws_mig) != fx.FXMIG_OK:
+        raise RuntimeError("per-depth form: device status " + fx.fxmig_strerror(fx.fxmig_check(b.ws_mig)))
+    ms, mig = [], []
+    for _ in range(steps):
+        slab.copy_(slab0)
+        flush.fill_(1)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        fx.fxmig_migrate_ex(d, lc, slab, b.vel, b.table, partials, 0, d.nz, b.ws_mig)
+        e1.record(stream)
+        fx.fxmig_image(d, partials, image)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e2))
+        mig.append(e0.elapsed_time(e1))
+    return {"ms_per_step": float(np.mean(ms)), "migrate_ms": float(np.mean(mig)), "partials": nparts,
+            "launches_per_step": 2 + d.nz, "image": image.cpu().numpy()}
+
+
 # ------------------------------------------------------------ batched lines
 BATCH_NAME = "batched_64"
 
@@ -598,13 +634,15 @@ def run_native(args, w):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = world * w.points * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
 
-    learned, precs = None, {}
+    learned, precs, per_depth = None, {}, None
     if world == 1 and not args.no_forms:
         if d.L <= 15:
             learned = measure_learned(fx, d, b, slab0, args.steps, flush, train_steps=args.train_steps)
         for name in PREC_NAMES:
             precs[name] = measure_precision(fx, d, b, slab0, args.steps, flush, launch,
                                             getattr(fx, "FXMIG_PREC_" + name))
+        if args.mode != 2:
+            per_depth = measure_per_depth(fx, d, b, slab0, min(args.steps, 5), flush)
 
     if rank != 0:
         if world > 1:
@@ -667,6 +705,21 @@ def run_native(args, w):
                     + ("(taps as hi + lo)" if "SPLIT" in name else "") + ", FP32 arithmetic",
             "image_rel_l2_vs_fp64_oracle": rel(img_p, img_ref) if img_ref is not None else None,
             "image_rel_l2_vs_plain_gpu": rel(img_p, img_plain), **r}
+    if per_depth is not None:
+        img_d = per_depth.pop("image")
+        gbs = 16.0 * w.points / (per_depth["migrate_ms"] * 1e-3) / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        slab_mb = d.nw * d.nx * 8 / 1e6
+        forms["per_depth"] = {
+            "value": w.points / (per_depth["ms_per_step"] * 1e-3), "unit": "point*freq/s",
+            "speedup_vs_plain": w.points / (per_depth["ms_per_step"] * 1e-3) / value,
+            "what": "one Eq. 1 launch per depth row (k_migrate_step), wavefield read and written "
+                    "through L2/HBM every step",
+            "wavefield_gbs": gbs, "hbm_peak_gbs": hbm, "frac_of_hbm": gbs / hbm,
+            "note": f"algorithmic 16 B per point*freq; the {slab_mb:.1f} MB wavefield stays in the "
+                    "129 MB L2 between launches, so this form is L2- and launch-latency-bound here",
+            "image_rel_l2_vs_fp64_oracle": rel(img_d, img_ref) if img_ref is not None else None,
+            "image_rel_l2_vs_plain_gpu": rel(img_d, img_plain), **per_depth}
     if forms:
         line["forms"] = forms
     if learned is not None:

@@ -125,8 +125,8 @@ __device__ __forceinline__ void prefetch_taps(const typename TP::E* tp) {
 // One lane item: the 8 outputs of line s at local positions xl0..xl0+7,
 // extrapolated with the operator of the first output.  Returns the mask of
 // outputs whose own operator differs (the velocity changes inside the 8):
-// those are left unwritten for the fixup round, and their operator rows are
-// prefetched into L1 meanwhile; idx1 receives their operator when they all
+// the fixup round rewrites those, and their operator rows are prefetched
+// into L1 meanwhile; idx1 receives their operator when they all
 // share one (the usual single change), else -1.  With an imaging buffer
 // (imgz), the real parts of the current wavefield go there.
 template <int LT, class WS, class TP, bool kPairs>
@@ -171,14 +171,9 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, c
         for (int r = 0; r < 8; ++r)
             if (xl0 + r >= g.wv) res[r] = 0ull;
     }
-    typename WS::T* dst = nxt + (size_t)s * g.SP;
-    if (skip == 0) {
-        store8<LT, WS>(dst + (xl0 >> 3) * 10, res);
-    } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-            if (!((skip >> r) & 1u)) WS::st1(dst + phys(xl0 + r + LT), res[r]);
-    }
+    // all 8 outputs: those whose own operator differs (skip) are rewritten by
+    // the fixup round, which a __syncwarp orders after these stores
+    store8<LT, WS>(nxt + (size_t)s * g.SP + (xl0 >> 3) * 10, res);
     return skip;
 }
 
@@ -624,8 +619,10 @@ __device__ __forceinline__ void run_group(const MigrateArgs& a, int g, unsigned 
                 uint32_t mask = 0;
                 int idx1 = -1;
                 if (work) mask = main_item<LT, WS, TP, kPairs>(sc, s, xl0, cur, nxt, srow, qz, imgz, taps, idx1);
-                if (__any_sync(0xffffffffu, mask != 0u))
+                if (__any_sync(0xffffffffu, mask != 0u)) {
+                    __syncwarp();  // the main items' stores precede the fixups' rewrites
                     coop_fixups<LT, WS, TP, kPairs>(sc, mask, s, xl0, idx1, cur, nxt, srow, qz, taps, lane);
+                }
             }
         }
         // velocity rows are converted by the whole CTA one step ahead
