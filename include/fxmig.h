@@ -104,7 +104,9 @@ typedef struct fxmig_desc {
  *                  form (1, 2, 4 or 8), 0 = choose
  *   groups         frequency groups (CTA clusters) in the persistent form, or
  *                  frequency tiles in the per-depth form; 0 = choose
- *   warps          warps per CTA (persistent form), 0 = choose
+ *   warps          compute warps per CTA (persistent form, 1..12), 0 = choose;
+ *                  with cluster > 1 one more warp per CTA carries the halo
+ *                  exchange between the CTAs of a cluster
  *   precision      FXMIG_PREC_* (persistent form only; 0 = FP32) */
 typedef struct fxmig_launch {
     int mode, cluster, groups, warps, precision;
