@@ -201,6 +201,35 @@ def test_halo_strips(fx, L, prec):
     assert rel_l2(image, img_ref) < tol_i
 
 
+@pytest.mark.parametrize("nx", [192, 320, 1000])
+@pytest.mark.parametrize("L,prec", [(4, "FP32"), (12, "FP32"), (17, "FP32"), (20, "FP32"),
+                                    (12, "FP16_SPLIT"), (17, "FP16_SPLIT")])
+def test_edge_warp_clusters_of_eight(fx, nx, L, prec):
+    # Clusters of 8 CTAs: segments of 3 chunks (192 traces; at L = 17, 20
+    # the left and right edge chunks of a middle segment overlap and every
+    # chunk is an edge chunk), 5 chunks (320 traces; in 16-bit storage the
+    # padded line length breaks the strip alignment, so every halo output
+    # goes by its own st.async) and 16 chunks (1000 traces; the last segment
+    # runs past the line end).  The edge warp of every CTA computes the
+    # outputs next to its neighbours and feeds both sides.
+    w = small_layered(nx=nx, nz=24, L=L, seed=17, name=f"layered_{nx}")
+    v, refl, sec = layered_inputs(w)
+    pr = problem(w, v, sec)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    d = desc_of(fx, w, pr["k_max"])
+    launch = fx.Launch(mode=1, cluster=8, precision=getattr(fx, "FXMIG_PREC_" + prec))
+    try:
+        fx.fxmig_num_partials(d, launch)
+    except fx.FxmigError:
+        pytest.skip("no plan for this shape (segment narrower than the operator, or LT not compiled)")
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch, [0, 7, w.nz])
+    P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if prec == "FP32" else (1e-2, 1e-2)
+    assert rel_l2(slabs[-1], P_ref) < tol_s
+    assert rel_l2(image, img_ref) < tol_i
+
+
 def test_halo_strips_straddling_warps(fx):
     # 496 traces over clusters of 2: segments of 31 chunks (not a multiple
     # of 32, so the compute items of a line run across warp boundaries and
