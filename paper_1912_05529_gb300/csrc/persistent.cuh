@@ -177,6 +177,23 @@ __device__ __forceinline__ uint32_t main_item(const SegCtx& g, int s, int xl0, c
     return skip;
 }
 
+// Position of the n-th set bit (n >= 1, counted from bit 0) of m, which
+// has at least n set bits: a binary search on population counts, five
+// fixed steps.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n > c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // Warp-cooperative recomputation of the outputs flagged in each lane's
 // `mask` (line s, chunk at xl0; bit 0 is never set): the flagged outputs of
 // the whole warp are numbered by output position r, then by lane, from one
@@ -207,7 +224,7 @@ __device__ __forceinline__ void coop_fixups(const SegCtx& g, uint32_t mask, int 
 #pragma unroll
         for (int q = 2; q < 8; ++q)
             if (pre[q] <= it) { r = q; br = bal[q]; pr = pre[q]; }
-        const int owner = it < total ? (int)__fns(br, 0, it - pr + 1) : 0;
+        const int owner = it < total ? nth_set_bit(br, it - pr + 1) : 0;
         const int s_o = __shfl_sync(0xffffffffu, s, owner);
         const int x0_o = __shfl_sync(0xffffffffu, xl0, owner);
         const int i1_o = __shfl_sync(0xffffffffu, idx1, owner);
