@@ -117,6 +117,10 @@ def test_invalid_launch_choices(fx):
     d = _desc(fx)
     assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(mode=7))) == fx.FXMIG_EINVAL
     assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(cluster=3))) == fx.FXMIG_EINVAL
+    # warps counts compute warps, 1..12 (the edge warp of a cluster comes on top)
+    for w in (1, 12):
+        assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(mode=1, warps=w))) > 0
+    assert fx.lib().fxmig_num_partials(ctypes.byref(d), ctypes.byref(fx.Launch(mode=1, warps=13))) == fx.FXMIG_EINVAL
 
 
 def test_precision_choices(fx):
