@@ -168,6 +168,28 @@ def oracle_run(w: W.Workload, sec, vm, threads: int = 0):
     return time.perf_counter() - t0, P, img, cores
 
 
+def oracle_single_thread(w: W.Workload, sec, vm, target_points: float = 3e7):
+    """The FP64 oracle's depth loop on one host thread, on a bounded sample of
+    the workload: a contiguous block of frequencies (about target_points
+    points x frequencies) over the full line and all depth rows.  Returns
+    (point*freq/s, sample description)."""
+    import oracle as O
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    kmax = float(om[-1] / float(vm.min()))
+    table = O.design_operators(w.nk, kmax, w.dx, w.dz, w.L, w.theta_deg)
+    _, dk = O.k_grid(w.nk, kmax)
+    nws = max(1, min(w.nw, int(target_points // (w.nx * w.nz))))
+    j0 = (w.nw - nws) // 2
+    P0 = O.band_dft(sec.astype(np.float64), w.i0 + j0, nws)
+    q = O.q_values(om[j0:j0 + nws], dk)
+    t0 = time.perf_counter()
+    O.migrate(P0, vm, table, q, nthreads=1)
+    secs = time.perf_counter() - t0
+    return (w.nx * w.nz * nws / secs,
+            f"{nws} of {w.nw} frequencies (bins {w.i0 + j0}..{w.i0 + j0 + nws - 1}), all {w.nx} traces and "
+            f"{w.nz} depth rows, one thread, {secs:.2f} s")
+
+
 def run_reference(args, w):
     """The oracle on the host cores, same metric and workload; each step is a
     bounded sample: a contiguous block of frequencies over the full line and
@@ -688,9 +710,12 @@ def run_native(args, w):
         img_gpu = b.image.cpu().numpy()
         # b.slab now holds the wavefield after the last e2e run (same inputs)
         P_gpu = b.slab.cpu().numpy()
+        st_val, st_sample = oracle_single_thread(w, sec, vm)
         line["cpu_baseline"] = {"value": w.points / secs, "unit": "point*freq/s", "cores": cores,
                                 "kind": "oracle", "sample": "whole workload, FP64 depth loop (design and "
-                                "t->f excluded)", "seconds": secs}
+                                "t->f excluded)", "seconds": secs,
+                                "single_thread": {"value": st_val, "unit": "point*freq/s", "cores": 1,
+                                                  "sample": st_sample}}
         line["parity"] = {"image_rel_l2": float(np.linalg.norm(img_gpu - img_ref) / np.linalg.norm(img_ref)),
                           "final_slice_rel_l2": float(np.linalg.norm(P_gpu - P_ref) / np.linalg.norm(P_ref))}
     rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))
