@@ -122,7 +122,7 @@ def k_max_of(w: W.Workload, vm_min: float) -> float:
 
 # sources of the persistent depth-loop kernel (the traffic record is valid
 # only for the exact sources it was captured from)
-KERNEL_SOURCES = ("paper_1912_05529_gb300/csrc/migrate.cu", "paper_1912_05529_gb300/csrc/persistent.cuh",
+KERNEL_SOURCES = ("paper_1912_05529_gb300/csrc/migrate.cu", "paper_1912_05529_gb300/csrc/depth.cuh",
                   "paper_1912_05529_gb300/csrc/fir.cuh", "paper_1912_05529_gb300/csrc/fxmig_internal.cuh")
 
 
@@ -131,7 +131,7 @@ def kernel_traffic(workload: str):
     capture recorded under profiles/, or None if the kernel sources changed
     since that capture (or none exists for this workload)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"traffic_k_migrate_persistent_{workload}.json")
+    path = os.path.join(ROOT, "profiles", f"traffic_k_depth_{workload}.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -693,7 +693,7 @@ def run_native(args, w):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TOP/s (FP32 pipe)",
                      "frac": achieved / peak_tops,
                      "traffic": kernel_traffic(w.name) if args.mode != 2 else None,
-                     "kernel": "k_migrate_persistent" if args.mode != 2 else "k_migrate_step",
+                     "kernel": "k_depth" if args.mode != 2 else "k_migrate_step",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                      "ops_per_point": ops_per_point(w.L), "migrate_ms": mig_avg},
         "e2e": {"value": e2e_val, "unit": "point*freq/s",

@@ -50,6 +50,7 @@ extern "C" {
 #define FXMIG_ECUDA     -3  /* a CUDA call failed; see fxmig_last_error() */
 #define FXMIG_ETIMEOUT  -4  /* (device) a bounded wait inside a kernel gave up */
 #define FXMIG_EVELOCITY -5  /* (device) a velocity sample was not finite and > 0 */
+#define FXMIG_ERANGE    -6  /* (device) an image contribution exceeded the accumulator's range */
 
 /* Workspace kinds for fxmig_workspace_bytes(). */
 #define FXMIG_WS_T2F      1
@@ -126,10 +127,32 @@ const char *fxmig_last_error(void);
  * and must not be shared by calls that may run concurrently. */
 size_t fxmig_workspace_bytes(const fxmig_desc *d, int kind);
 
-/* Number of partial images fxmig_migrate_ex() writes for `d` and `launch`
- * (NULL = automatic choices); the partials buffer holds that many [nz][nx]
- * float images.  Returns a negative code if d is invalid. */
+/* Number of [nz][nx] float planes of the `partials` buffer that
+ * fxmig_migrate_ex() writes for `d` and `launch` (NULL = automatic choices).
+ * The buffer is an image accumulator in fixed point (3 planes for every form:
+ * int64 rows and their scale exponents), read by fxmig_image.  Returns a
+ * negative code if d or launch is invalid. */
 int fxmig_num_partials(const fxmig_desc *d, const fxmig_launch *launch);
+
+/* The launch fxmig_migrate_ex() makes for `d` and `launch` (NULL = automatic):
+ *   mode            FXMIG_MODE_PERSISTENT or FXMIG_MODE_PER_DEPTH
+ *   cluster         CTAs per frequency group (persistent: 1, or a cluster of 2
+ *                   that splits the group's lines laid end to end into halves)
+ *   groups          frequency groups (per-depth form: frequency tiles)
+ *   ctas            CTAs of the depth-loop launch (groups * cluster; per-depth
+ *                   form: per launch)
+ *   warps           compute warps per CTA (persistent: plus one warp when a
+ *                   group has a line cut between the two CTAs of its cluster)
+ *   items_per_lane  8-output items per compute lane and depth step (1 or 2)
+ *   waves           ctas over the CTAs the GPU holds at once
+ *   smem_bytes      dynamic shared memory per CTA
+ * The paper has no counterpart (its launch is one thread per output point).
+ * Errors: FXMIG_EINVAL. */
+typedef struct fxmig_shape {
+    int mode, cluster, groups, ctas, warps, items_per_lane, waves;
+    size_t smem_bytes;
+} fxmig_shape;
+int fxmig_launch_shape(const fxmig_desc *d, const fxmig_launch *launch, fxmig_shape *out);
 
 /* Operator table design (Sec. II: the filter design is an optimisation
  * between short and long filters; Sec. III: filters designed in advance and

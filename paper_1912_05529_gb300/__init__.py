@@ -20,11 +20,12 @@ import math
 import os
 
 __all__ = [
-    "FXMIG_OK", "FXMIG_EINVAL", "FXMIG_ENOSPC", "FXMIG_ECUDA", "FXMIG_ETIMEOUT", "FXMIG_EVELOCITY",
+    "FXMIG_OK", "FXMIG_EINVAL", "FXMIG_ENOSPC", "FXMIG_ECUDA", "FXMIG_ETIMEOUT", "FXMIG_EVELOCITY", "FXMIG_ERANGE",
     "FXMIG_WS_T2F", "FXMIG_WS_MIGRATE", "FXMIG_WS_MLP_MIGRATE", "FXMIG_PREC_FP32", "FXMIG_PREC_FP16",
     "FXMIG_PREC_BF16", "FXMIG_PREC_FP16_SPLIT", "FXMIG_PREC_BF16_SPLIT", "FXMIG_MODE_AUTO", "FXMIG_MODE_PERSISTENT", "FXMIG_MODE_PER_DEPTH",
     "FxmigError", "Desc", "Launch", "lib", "library_path",
-    "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials",
+    "fxmig_version", "fxmig_strerror", "fxmig_workspace_bytes", "fxmig_num_partials", "Shape",
+    "fxmig_launch_shape",
     "fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_migrate_ex", "fxmig_image",
     "fxmig_check", "fxmig_migrate_noalloc", "fxmig_selftest_timeout", "desc_for", "migrate_section",
     "fxmig_mlp_param_count", "fxmig_mlp_train_ws_bytes", "fxmig_design_at", "fxmig_mlp_train",
@@ -33,7 +34,8 @@ __all__ = [
     "fxmig_batch_autotune", "fxmig_migrate_batch",
 ]
 
-FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY = 0, -1, -2, -3, -4, -5
+FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY, FXMIG_ERANGE = \
+    0, -1, -2, -3, -4, -5, -6
 FXMIG_WS_T2F, FXMIG_WS_MIGRATE, FXMIG_WS_MLP_MIGRATE = 1, 2, 3
 FXMIG_PREC_FP32, FXMIG_PREC_FP16, FXMIG_PREC_BF16, FXMIG_PREC_FP16_SPLIT, FXMIG_PREC_BF16_SPLIT = 0, 1, 2, 3, 4
 FXMIG_MODE_AUTO, FXMIG_MODE_PERSISTENT, FXMIG_MODE_PER_DEPTH = 0, 1, 2
@@ -74,6 +76,16 @@ class BatchPlan(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int), ("lines_cap", ctypes.c_int)]
 
 
+class Shape(ctypes.Structure):
+    """Mirror of ``fxmig_shape`` (the launch fxmig_migrate_ex makes)."""
+    _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("warps", ctypes.c_int), ("items_per_lane", ctypes.c_int),
+                ("waves", ctypes.c_int), ("smem_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class Launch(ctypes.Structure):
     """Mirror of ``fxmig_launch`` (zeros = automatic)."""
     _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
@@ -98,6 +110,8 @@ def lib():
         L.fxmig_workspace_bytes.restype = sz
         L.fxmig_num_partials.argtypes = [pd, pl]
         L.fxmig_num_partials.restype = i
+        L.fxmig_launch_shape.argtypes = [pd, pl, ctypes.POINTER(Shape)]
+        L.fxmig_launch_shape.restype = i
         L.fxmig_design_operators.argtypes = [pd, vp, vp, vp]
         L.fxmig_t2f.argtypes = [pd, vp, vp, vp, sz, vp]
         L.fxmig_migrate.argtypes = [pd, vp, vp, vp, vp, i, i, i, vp, sz, vp]
@@ -188,6 +202,14 @@ def fxmig_num_partials(d: Desc, launch: Launch | None = None) -> int:
     return n
 
 
+def fxmig_launch_shape(d: Desc, launch: Launch | None = None) -> Shape:
+    """The launch fxmig_migrate_ex makes for d and launch (None = automatic)."""
+    out = Shape()
+    _check(lib().fxmig_launch_shape(ctypes.byref(d), ctypes.byref(launch) if launch else None, ctypes.byref(out)),
+           "fxmig_launch_shape")
+    return out
+
+
 def fxmig_design_operators(d: Desc, table, table64=None, stream=None) -> None:
     """table: [nk][L+1] complex64 (device); table64: [nk][L+1] complex128 or None."""
     torch = _torch()
@@ -228,7 +250,8 @@ def fxmig_migrate_ex(d: Desc, launch: Launch | None, slab, vel, table, partials,
 
 def fxmig_migrate(d: Desc, slab, vel, table, partials, z_begin, z_end, ws, stream=None) -> None:
     """slab: [nw][nx] complex64 in/out; vel: [nz][nx] float32; table: [nk][L+1]
-    complex64; partials: [nparts][nz][nx] float32; ws: uint8 scratch."""
+    complex64; partials: [nparts][nz][nx] float32, the image accumulator
+    (fixed-point rows, read by fxmig_image); ws: uint8 scratch."""
     fxmig_migrate_ex(d, None, slab, vel, table, partials, z_begin, z_end, ws, stream)
 
 

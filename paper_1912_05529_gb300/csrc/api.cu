@@ -61,6 +61,10 @@ static int cuda_fail(cudaError_t e, const char* where) {
     return FXMIG_ECUDA;
 }
 
+namespace fxmig_impl {
+int record_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}  // namespace fxmig_impl
+
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 extern "C" {
@@ -75,6 +79,7 @@ const char* fxmig_strerror(int code) {
         case FXMIG_ECUDA: return "CUDA error";
         case FXMIG_ETIMEOUT: return "a bounded wait on the device gave up";
         case FXMIG_EVELOCITY: return "velocity sample not finite and positive";
+        case FXMIG_ERANGE: return "image contribution beyond the accumulator's range";
         default: return "unknown error";
     }
 }
@@ -94,6 +99,36 @@ int fxmig_num_partials(const fxmig_desc* d, const fxmig_launch* launch) {
     MigratePlan p;
     const int rc = plan_migrate(d, launch, &p);
     return rc == FXMIG_OK ? p.nparts : rc;
+}
+
+int fxmig_launch_shape(const fxmig_desc* d, const fxmig_launch* launch, fxmig_shape* out) {
+    if (!desc_valid(d) || !out) return FXMIG_EINVAL;
+    MigratePlan p;
+    const int rc = plan_migrate(d, launch, &p);
+    if (rc != FXMIG_OK) return rc;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    out->mode = p.mode;
+    out->cluster = p.cluster;
+    out->groups = p.groups;
+    if (p.mode == FXMIG_MODE_PER_DEPTH) {
+        out->ctas = p.groups * ((d->nx + 255) / 256);
+        out->warps = p.warps;
+        out->items_per_lane = 1;
+        out->waves = 1;
+    } else {
+        out->ctas = p.groups * p.cluster;
+        out->warps = p.warps;
+        out->items_per_lane = p.nr;
+        const int resident = p.cluster == 1 ? sms : 2 * (sms / 2);
+        out->waves = (out->ctas + resident - 1) / resident;
+    }
+    out->smem_bytes = p.smem;
+    return FXMIG_OK;
 }
 
 int fxmig_design_operators(const fxmig_desc* d, void* table, void* table64, void* stream) {
@@ -124,7 +159,7 @@ int fxmig_migrate_ex(const fxmig_desc* d, const fxmig_launch* launch, void* slab
     if (nparts < plan.nparts || ws_bytes < migrate_ws_bytes(d)) return FXMIG_ENOSPC;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (z_begin == z_end) {
-        const cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), s);
+        const cudaError_t e = cudaMemsetAsync(ws, 0, 16, s);
         return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_migrate");
     }
     const cudaError_t e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s, true);
@@ -137,8 +172,9 @@ int fxmig_migrate(const fxmig_desc* d, void* slab, const float* vel, const void*
 }
 
 int fxmig_image(const fxmig_desc* d, const float* partials, int nparts, float* image, void* stream) {
-    if (!desc_valid(d) || !partials || !image || nparts < 0) return FXMIG_EINVAL;
-    if (!aligned(partials, 4) || !aligned(image, 4)) return FXMIG_EINVAL;
+    if (!desc_valid(d) || !partials || !image) return FXMIG_EINVAL;
+    if (!aligned(partials, 16) || !aligned(image, 4)) return FXMIG_EINVAL;
+    if (nparts < image_planes(d->nx)) return FXMIG_ENOSPC;
     const cudaError_t e = launch_image(d, partials, nparts, image, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FXMIG_OK : cuda_fail(e, "fxmig_image");
 }
@@ -213,7 +249,7 @@ int fxmig_mlp_num_partials(const fxmig_desc* d) {
 int fxmig_mlp_migrate(const fxmig_desc* d, void* slab, const float* vel, const float* params, float* partials,
                       int nparts, int z_begin, int z_end, void* ws, size_t ws_bytes, void* stream) {
     if (!desc_valid(d) || !slab || !vel || !params || !partials || !ws) return FXMIG_EINVAL;
-    if (!aligned(slab, 8) || !aligned(vel, 4) || !aligned(params, 4) || !aligned(partials, 4) || !aligned(ws, 256))
+    if (!aligned(slab, 8) || !aligned(vel, 4) || !aligned(params, 4) || !aligned(partials, 16) || !aligned(ws, 256))
         return FXMIG_EINVAL;
     if (z_begin < 0 || z_end < z_begin || z_end > d->nz) return FXMIG_EINVAL;
     MlpMigratePlan plan;
@@ -282,6 +318,7 @@ int fxmig_check(const void* ws, void* stream) {
     if (e != cudaSuccess) return cuda_fail(e, "fxmig_check");
     if (status & kStatusTimeout) return FXMIG_ETIMEOUT;
     if (status & kStatusVelocity) return FXMIG_EVELOCITY;
+    if (status & kStatusOverflow) return FXMIG_ERANGE;
     return FXMIG_OK;
 }
 

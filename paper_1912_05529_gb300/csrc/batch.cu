@@ -1,48 +1,49 @@
 // batch.cu -- many independent 2-D lines (uneven Nx, Nz, band and L) in one
 // persistent launch (the depth loop of Algorithm 1 for every line).
 //
-// A line's frequencies are split into groups (as many lines as fit one CTA's
-// shared memory), and its groups into a few streams, sized so that the batch
-// has about four streams per cluster.  Work items are (line, stream) pairs.
-// One kernel launch keeps one CTA cluster per group of SMs; each cluster
-// takes the next item from a device counter (largest items first) and runs
-// the whole depth loop of each group of that stream in turn (run_group of
-// the persistent form), adding the groups' image rows into the stream's
-// partial image in a fixed order (deterministic), then takes the next item.
-// The per-line arguments travel in the kernel parameters, so the launch needs
-// no host-to-device copy and can be captured into a CUDA graph.
+// A line's frequencies are split into groups (as many lines as one CTA pair
+// holds, or at most a cap); a work item is one (line, group).  One kernel
+// launch keeps one CTA cluster per pair of SMs (or one CTA per SM); each
+// cluster takes the next item from a device counter (items ordered largest
+// first) and runs the whole depth loop of that group (run_depth of the
+// persistent form, with the line's own half-length by a run-time switch over
+// the compiled lengths), then takes the next item.  Every group adds its image
+// rows into its line's fixed-point accumulator (image.cu), so the image does
+// not depend on which cluster ran which group.  The per-line arguments travel
+// in the kernel parameters, so the launch needs no host-to-device copy and
+// can be captured into a CUDA graph.
 //
-// Planning: a cluster size C for the launch and, per line, the segment width
-// W = nx / C and the frequency lines per group (as many as fit shared memory,
-// or at most a cap).  The autotuner times a few (C, cap) candidates on scratch
-// copies of the wavefields over the first depth steps and keeps the fastest.
+// Planning: a cluster size C (1 or 2) for the launch and, per line, the
+// frequency lines per group.  The autotuner times a few (C, cap) candidates on
+// scratch copies of the wavefields over the first depth rows of every line and
+// keeps the fastest.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
-#include "persistent.cuh"
+#include "depth.cuh"
 
 namespace fxmig_impl {
 
-// 12 warps: with clusters of 2 or more CTAs, 11 compute warps and the edge
-// warp of the depth loop (run_group); clusters of 1 compute with all 12.
-// Twelve warps keep 168 registers per thread (three warps per SM
-// sub-partition), which the batch kernel's switch over the compiled
-// half-lengths needs more than a thirteenth warp (measured on the 64-line
-// batch: 530 ms against 570 ms).
-constexpr int kBatchWarps = kPersistentMaxWarps;
+// The batch kernel carries two 8-output items per compute lane (8 compute
+// warps + the extra warp): one launch then fits groups of up to 512 chunks
+// per CTA, which lines up to 8192 traces need (half a line per CTA).
+constexpr int kBatchNR = 2;
+constexpr int kBatchComputeWarps = DepthWarps<kBatchNR>::kMaxCompute;
 
 struct BatchLineArgs {
-    MigrateArgs a;
+    DepthArgs a;
     int LT;
-    int P;                // streams of the line (its partial images)
     const float2* table;  // the line's public [nk][L+1] table (expanded into a.taps)
+    const float* vel;     // the line's velocity [nz][nx] (converted into a.slow)
+    double* norms;        // [nw] frequency norms of the line's wavefield (image scale)
+    int* head;            // the line's scale exponent (= a.scale_exp) and norm counter
 };
 struct BatchArgs {
     int nlines, nitems;
-    int* counter;                            // work-queue head, zero at launch
-    int order[FXMIG_BATCH_MAX_LINES];        // lines in the order their items are handed out
-    int item_base[FXMIG_BATCH_MAX_LINES + 1];  // first item (stream) of line order[k]
+    int* counter;                              // work-queue head, zero at launch
+    int order[FXMIG_BATCH_MAX_LINES];          // lines in the order their items are handed out
+    int item_base[FXMIG_BATCH_MAX_LINES + 1];  // first item (group) of line order[k]
     BatchLineArgs line[FXMIG_BATCH_MAX_LINES];
 };
 
@@ -50,13 +51,7 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, int v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" :: "r"(addr), "r"(v) : "memory");
 }
 
-template <int LT>
-__device__ __forceinline__ void run_item_lt(const MigrateArgs& a, int g, unsigned char* smem, int part,
-                                            bool accumulate) {
-    run_group<LT, WsF32, TapF32>(a, g, smem, part, accumulate);
-}
-
-__global__ void __launch_bounds__(kBatchWarps * 32, 1) k_migrate_batch(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(DepthWarps<kBatchNR>::kThreads, 1) k_migrate_batch(const __grid_constant__ BatchArgs b) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_item;
     const int C = b.line[0].a.C;  // the launch's cluster size (the same for every line)
@@ -77,38 +72,33 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_migrate_batch(const __g
         int k = 0;
         while (b.item_base[k + 1] <= item) ++k;
         const BatchLineArgs& L = b.line[b.order[k]];
-        const int p = item - b.item_base[k];  // the line's stream
-        const int g0 = (int)(((long long)p * L.a.G) / L.P), g1 = (int)(((long long)(p + 1) * L.a.G) / L.P);
-        for (int g = g0; g < g1; ++g) {
-            // the groups of stream p add their rows into partial image p
-            // (the line's arguments are read in place from the parameters)
-            const bool acc = g > g0;
-            switch (L.LT) {
-                case 4: run_item_lt<4>(L.a, g, smem, p, acc); break;
-                case 8: run_item_lt<8>(L.a, g, smem, p, acc); break;
-                case 12: run_item_lt<12>(L.a, g, smem, p, acc); break;
-                case 16: run_item_lt<16>(L.a, g, smem, p, acc); break;
-                case 17: run_item_lt<17>(L.a, g, smem, p, acc); break;
-                case 20: run_item_lt<20>(L.a, g, smem, p, acc); break;
-                default: break;
-            }
-            // the next group reuses the shared memory: every CTA of the
-            // cluster has finished this one (write-back included)
-            if (C > 1) cluster_sync_all(); else __syncthreads();
+        const int g = item - b.item_base[k];
+        switch (L.LT) {
+            case 4: run_depth<4, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            case 8: run_depth<8, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            case 12: run_depth<12, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            case 16: run_depth<16, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            case 17: run_depth<17, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            case 20: run_depth<20, WsF32, TapF32, kBatchNR, false>(L.a, g, smem); break;
+            default: break;
         }
         // s_item is rewritten for the next item only after every CTA of the
-        // cluster has passed the last group's final barrier (above)
+        // cluster has finished this one (run_depth ends with a cluster barrier)
+        if (C > 1) cluster_sync_all(); else __syncthreads();
     }
 }
 
-// Expand every line's [nk][L+1] table into its kernel layout (TapF32).
-__global__ void k_expand_taps_batch(const __grid_constant__ BatchArgs b) {
+// Per-line preparation of a batch, grid.y over lines: the table in the
+// kernel's tap layout, the slowness field of the line's rows, zeroed
+// accumulator rows.
+__global__ void k_batch_prep(const __grid_constant__ BatchArgs b) {
     for (int li = blockIdx.y; li < b.nlines; li += gridDim.y) {
-        const MigrateArgs& a = b.line[li].a;
+        const DepthArgs& a = b.line[li].a;
         const int LT = b.line[li].LT, L = a.L;
         float4* taps = static_cast<float4*>(const_cast<void*>(a.taps));
         const int n = a.nk * (LT + 1);
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+        for (int i = gtid; i < n; i += gstride) {
             const int kk = i / (LT + 1), t = i - kk * (LT + 1);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (t <= L) {
@@ -117,7 +107,79 @@ __global__ void k_expand_taps_batch(const __grid_constant__ BatchArgs b) {
             }
             taps[i] = v;
         }
+        const float* vel = b.line[li].vel;
+        float* slow = const_cast<float*>(a.slow);
+        const size_t ns = (size_t)(a.z_end - a.z_begin) * a.nxp;
+        bool bad = false;
+        for (size_t i = gtid; i < ns; i += gstride) {
+            const int z = a.z_begin + (int)(i / (size_t)a.nxp);
+            const int x = (int)(i % (size_t)a.nxp);
+            const float v = vel[(size_t)z * a.nx + (x < a.nx ? x : a.nx - 1)];
+            if (x < a.nx) bad |= !(v > 0.f && v <= FLT_MAX);
+            slow[(size_t)z * a.nxp + x] = __frcp_rn(v);
+        }
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.status, kStatusVelocity);
+        const size_t na = (size_t)(a.z_end - a.z_begin) * a.nxp;
+        for (size_t i = gtid; i < na; i += gstride) a.acc[(size_t)a.z_begin * a.nxp + i] = 0ull;
     }
+}
+
+// Per-line image scale (grid.y over lines, grid.x over frequency lines):
+// ||P(., w)||_2 per frequency, and the line's last block picks e from the
+// largest of them, as in image.cu.
+__global__ void __launch_bounds__(256) k_batch_norms(const __grid_constant__ BatchArgs b) {
+    __shared__ double red[256];
+    __shared__ bool last;
+    const int li = blockIdx.y;
+    if (li >= b.nlines) return;
+    const DepthArgs& a = b.line[li].a;
+    if ((int)blockIdx.x >= a.nw) return;
+    double* norms = b.line[li].norms;
+    int* head = b.line[li].head;
+    const float2* p = a.slab + (size_t)blockIdx.x * a.nx;
+    double s = 0.0;
+    for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+        const float2 v = p[x];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        norms[blockIdx.x] = sqrt(red[0]);
+        __threadfence();
+        last = atomicAdd(&head[1], 1) == a.nw - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __shared__ int e_sh;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        double B = 0.0;
+        for (int j = 0; j < a.nw; ++j) B = fmax(B, *((volatile const double*)(norms + j)));
+        int e = 0;
+        if (B > 0.0 && B <= 1.0e300) {
+            int k;
+            frexp(B, &k);  // the largest frequency norm < 2^k
+            e = 23 - k;
+        }
+        e = e < -126 ? -126 : (e > 127 ? 127 : e);
+        // a continued depth range keeps the previous rows' exponent (image.cu)
+        const int* e_prev = reinterpret_cast<const int*>(a.acc + (size_t)a.nz * a.nxp);
+        if (a.z_begin > 0) {
+            const int ep = e_prev[a.z_begin - 1];
+            if (ep >= e - 4 && ep <= e + 4) e = ep;
+        }
+        e_sh = e;
+        head[0] = e;
+        head[1] = 0;
+    }
+    __syncthreads();
+    int* e_rows = reinterpret_cast<int*>(a.acc + (size_t)a.nz * a.nxp);
+    for (int z = a.z_begin + (int)threadIdx.x; z < a.z_end; z += blockDim.x) e_rows[z] = e_sh;
 }
 
 // ------------------------------------------------------------------ host side
@@ -140,60 +202,81 @@ int smem_optin() {
 size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct LinePlan {
-    int LT, W, lines, G, img;
+    int LT, G, ncw, extra;
     size_t smem;
-    double cost;  // work of one group: points x frequencies x FP32 operations
+    double cost;  // work of one group: chunks of its busiest CTA x depth rows x FP32 operations
 };
 
 // Per-line choices for cluster size C and lines-per-group cap (0 = as many
-// as fit).  Returns false if some line cannot be planned.
+// as fit).  Returns false if the line cannot be planned.
 bool plan_line(const fxmig_desc* d, int C, int cap, int smax, LinePlan* p) {
     const int LT = compiled_half_length(d->L);
     if (LT < 0) return false;
-    int W = (d->nx + C - 1) / C;
-    W = (W + 7) & ~7;
-    if (C > 1 && W < LT) return false;
-    int fit = 0;
-    while (fit < d->nw && persistent_layout(W, fit + 1, LT, 8, false).total <= (size_t)smax) ++fit;
-    if (fit == 0) return false;
-    int m = cap > 0 ? std::min(cap, fit) : fit;
-    const int G = (d->nw + m - 1) / m;
-    m = (d->nw + G - 1) / G;  // balanced lines per group
-    p->LT = LT;
-    p->W = W;
-    p->lines = m;
-    p->G = G;
-    p->img = persistent_layout(W, m, LT, 8, true).total <= (size_t)smax ? 1 : 0;
-    p->smem = persistent_layout(W, m, LT, 8, p->img != 0).total;
-    p->cost = (double)m * W * C * (double)d->nz * (6.0 * LT + 4.0);
-    return true;
+    const int nxp = slow_pitch(d->nx);
+    const int mcap = std::min(d->nw, cap > 0 ? cap : 2 * kDepthMaxSegs - 2);
+    for (int m = mcap; m >= 1; --m) {
+        const int G = (d->nw + m - 1) / m;
+        int maxch = 0, cut = 0;
+        size_t smem = 0;
+        bool ok = true;
+        DepthLayout L;
+        for (int g = 0; g < G && ok; ++g)
+            for (int r = 0; r < C && ok; ++r) {
+                ok = depth_layout(d->nx, nxp, d->nw, G, C, g, r, LT, 8, L);
+                if (!ok) break;
+                maxch = std::max(maxch, L.nchunks);
+                cut |= L.cutseg >= 0 ? 1 : 0;
+                smem = std::max(smem, L.total);
+            }
+        if (!ok || smem > (size_t)smax || maxch == 0 || maxch > 32 * kBatchNR * kBatchComputeWarps) continue;
+        p->LT = LT;
+        p->G = G;
+        p->ncw = std::max(1, (maxch + 32 * kBatchNR - 1) / (32 * kBatchNR));
+        p->extra = (C > 1 && cut) ? 1 : 0;
+        p->smem = smem;
+        p->cost = (double)maxch * d->nz * (6.0 * LT + 4.0);
+        return true;
+    }
+    return false;
 }
-
-struct BatchLayout {
-    size_t status, taps_off[FXMIG_BATCH_MAX_LINES], scratch, total;
-};
 
 // Depth rows of a line that the autotuner runs: an eighth of the line (at
 // least 8), so the items keep the proportions of the full run.
 int tune_rows(const fxmig_desc& d) { return std::min(d.nz, std::max(8, (d.nz + 7) / 8)); }
 
-// Workspace: status word and queue counter, expanded tables, and
-// (autotuner, pmax != nullptr) scratch wavefields and pmax[i] partial images
-// of the tuning rows per line.
-BatchLayout batch_layout(const fxmig_line* lines, int n, const int* pmax) {
+// Workspace: status word and queue counter; per-line heads (scale exponent,
+// norm counter); per line the expanded table, the slowness field and the
+// frequency norms; (autotuner) scratch wavefields and accumulators of the
+// tuning rows.
+struct BatchLayout {
+    size_t heads, norm_off[FXMIG_BATCH_MAX_LINES], taps_off[FXMIG_BATCH_MAX_LINES],
+        slow_off[FXMIG_BATCH_MAX_LINES], norms, scratch, total;
+};
+BatchLayout batch_layout(const fxmig_line* lines, int n, bool scratch) {
     BatchLayout L = {};
     size_t o = kStatusBytes;
+    L.heads = o;
+    o += r256((size_t)n * 16);
+    L.norms = o;
+    long long nn = 0;
+    for (int i = 0; i < n; ++i) {
+        L.norm_off[i] = (size_t)nn;
+        nn += lines[i].d.nw;
+    }
+    o += r256((size_t)nn * 8);
     for (int i = 0; i < n; ++i) {
         const int LT = compiled_half_length(lines[i].d.L);
         L.taps_off[i] = o;
         o += r256((size_t)lines[i].d.nk * (LT + 1) * 16);
+        L.slow_off[i] = o;
+        o += r256((size_t)lines[i].d.nz * slow_pitch(lines[i].d.nx) * 4);
     }
     L.scratch = o;
-    if (pmax) {
+    if (scratch) {
         for (int i = 0; i < n; ++i) {
             const fxmig_desc& d = lines[i].d;
-            o += r256((size_t)d.nw * d.nx * 8);                            // wavefield copy
-            o += r256((size_t)pmax[i] * tune_rows(d) * d.nx * 4);          // partial rows
+            o += r256((size_t)d.nw * d.nx * 8);                                  // wavefield copy
+            o += r256((size_t)image_planes(d.nx) * tune_rows(d) * d.nx * 4);    // accumulator rows
         }
     }
     L.total = o;
@@ -223,68 +306,35 @@ bool batch_lines_valid(const fxmig_line* lines, int n) {
 }
 
 namespace {
-bool plan_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, std::vector<LinePlan>* lp,
-                std::vector<int>* P);
+bool plan_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, std::vector<LinePlan>* lp) {
+    const int C = plan.cluster;
+    if (C != 1 && C != 2) return false;
+    const int smax = smem_optin();
+    lp->assign(n, LinePlan());
+    for (int i = 0; i < n; ++i)
+        if (!plan_line(&lines[i].d, C, plan.lines_cap, smax, &(*lp)[i])) return false;
+    return true;
+}
 
-// The autotuner's candidate plans: cluster sizes 1, 2, 4, 8, each with as
-// many lines per group as fit and with half of what fits on the widest line.
+// The autotuner's candidate plans: cluster sizes 2 and 1, each with as many
+// lines per group as fit and with a cap of half of what fits on the
+// narrowest line.
 std::vector<fxmig_batch_plan> tune_candidates(const fxmig_line* lines, int n) {
     std::vector<fxmig_batch_plan> out;
-    for (int C : {1, 2, 4, 8}) {
+    for (int C : {2, 1}) {
         std::vector<LinePlan> lp;
-        std::vector<int> P;
         const fxmig_batch_plan p0 = {C, 0};
-        if (!plan_batch(lines, n, p0, &lp, &P)) continue;
+        if (!plan_batch(lines, n, p0, &lp)) continue;
         out.push_back(p0);
         int fit_min = 1 << 30;
-        for (int i = 0; i < n; ++i) fit_min = std::min(fit_min, lp[i].lines);
+        for (int i = 0; i < n; ++i) fit_min = std::min(fit_min, (lines[i].d.nw + lp[i].G - 1) / lp[i].G);
         if (fit_min >= 2) out.push_back(fxmig_batch_plan{C, fit_min / 2});
     }
     return out;
 }
-
-// Largest stream count of every line over the candidates.
-std::vector<int> tune_pmax(const fxmig_line* lines, int n) {
-    std::vector<int> pmax(n, 1);
-    for (const fxmig_batch_plan& p : tune_candidates(lines, n)) {
-        std::vector<LinePlan> lp;
-        std::vector<int> P;
-        if (!plan_batch(lines, n, p, &lp, &P)) continue;
-        for (int i = 0; i < n; ++i) pmax[i] = std::max(pmax[i], P[i]);
-    }
-    return pmax;
-}
 }  // namespace
 
-size_t batch_ws_bytes(const fxmig_line* lines, int n, bool scratch) {
-    if (!scratch) return batch_layout(lines, n, nullptr).total;
-    const std::vector<int> pmax = tune_pmax(lines, n);
-    return batch_layout(lines, n, pmax.data()).total;
-}
-
-namespace {
-// Line plans and stream counts of a batch: about four streams per cluster,
-// each line's share in proportion to its work.
-bool plan_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, std::vector<LinePlan>* lp,
-                std::vector<int>* P) {
-    const int C = plan.cluster;
-    if (C != 1 && C != 2 && C != 4 && C != 8) return false;
-    const int smax = smem_optin();
-    lp->assign(n, LinePlan());
-    P->assign(n, 1);
-    double total = 0.0;
-    for (int i = 0; i < n; ++i) {
-        if (!plan_line(&lines[i].d, C, plan.lines_cap, smax, &(*lp)[i])) return false;
-        total += (*lp)[i].cost * (*lp)[i].G;
-    }
-    const double target = total / (4.0 * std::max(1, sms_of_device() / C));
-    for (int i = 0; i < n; ++i) {
-        const double w = (*lp)[i].cost * (*lp)[i].G;
-        (*P)[i] = std::max(1, std::min((*lp)[i].G, (int)std::lround(w / target)));
-    }
-    return true;
-}
-}  // namespace
+size_t batch_ws_bytes(const fxmig_line* lines, int n, bool scratch) { return batch_layout(lines, n, scratch).total; }
 
 int batch_num_partials(const fxmig_line* lines, int n, const fxmig_batch_plan* plan, int* out) {
     fxmig_batch_plan p = {2, 0};
@@ -293,78 +343,84 @@ int batch_num_partials(const fxmig_line* lines, int n, const fxmig_batch_plan* p
         if (p.cluster == 0) p.cluster = 2;
     }
     std::vector<LinePlan> lp;
-    std::vector<int> P;
-    if (!plan_batch(lines, n, p, &lp, &P)) return FXMIG_EINVAL;
-    for (int i = 0; i < n; ++i) out[i] = P[i];
+    if (!plan_batch(lines, n, p, &lp)) return FXMIG_EINVAL;
+    for (int i = 0; i < n; ++i) out[i] = image_planes(lines[i].d.nx);
     return FXMIG_OK;
 }
 
 // Fill the launch arguments for plan; with slabs != nullptr (autotuner)
-// every line runs on a scratch wavefield and scratch partial rows over its
+// every line runs on a scratch wavefield and scratch accumulator over its
 // first tune_rows depth rows.
 static int fill_args(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, unsigned char* wsb,
-                     BatchArgs* b, size_t* smem_max, const std::vector<float2*>* slabs,
-                     const std::vector<float*>* partials) {
+                     BatchArgs* b, size_t* smem_max, int* warps, const std::vector<float2*>* slabs,
+                     const std::vector<float*>* accs) {
     const int C = plan.cluster;
-    const BatchLayout Lw = batch_layout(lines, n, nullptr);
+    const BatchLayout Lw = batch_layout(lines, n, false);
     std::vector<LinePlan> lp;
-    std::vector<int> P;
-    if (!plan_batch(lines, n, plan, &lp, &P)) return FXMIG_EINVAL;
+    if (!plan_batch(lines, n, plan, &lp)) return FXMIG_EINVAL;
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    // largest streams first
-    auto stream_cost = [&](int i) { return lp[i].cost * lp[i].G / P[i]; };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return stream_cost(x) > stream_cost(y); });
+    // largest groups first
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lp[x].cost > lp[y].cost; });
     b->nlines = n;
     b->counter = reinterpret_cast<int*>(wsb + sizeof(int));
     b->item_base[0] = 0;
     *smem_max = 0;
+    int ncw = 1, extra = 0;
+    for (int i = 0; i < n; ++i) {
+        ncw = std::max(ncw, lp[i].ncw);
+        extra |= lp[i].extra;
+    }
+    *warps = ncw + extra;
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         b->order[k] = i;
-        b->item_base[k + 1] = b->item_base[k] + P[i];
+        b->item_base[k + 1] = b->item_base[k] + lp[i].G;
         *smem_max = std::max(*smem_max, lp[i].smem);
         const fxmig_desc& d = lines[i].d;
-        MigrateArgs a = {};
-        a.nx = d.nx; a.nz = d.nz; a.nw = d.nw; a.nk = d.nk; a.i0 = d.i0; a.nt = d.nt; a.L = d.L;
+        DepthArgs a = {};
+        a.nx = d.nx; a.nxp = slow_pitch(d.nx); a.nz = d.nz; a.nw = d.nw; a.nk = d.nk; a.L = d.L;
+        a.i0 = d.i0; a.nt = d.nt;
         a.z_begin = lines[i].z_begin;
         a.z_end = lines[i].z_end;
         a.dt = d.dt;
         a.dk = d.nk > 1 ? d.k_max / (double)(d.nk - 1) : 0.0;
         a.slab = static_cast<float2*>(lines[i].slab);
-        a.vel = lines[i].vel;
-        a.slow = nullptr;  // slowness rows converted inside the depth loop
+        a.slow = reinterpret_cast<const float*>(wsb + Lw.slow_off[i]);
         a.taps = wsb + Lw.taps_off[i];
-        a.partials = lines[i].partials;
+        a.acc = reinterpret_cast<unsigned long long*>(lines[i].partials);
+        int* head = reinterpret_cast<int*>(wsb + Lw.heads) + 4 * i;
+        a.scale_exp = head;
         a.status = reinterpret_cast<int*>(wsb);
-        a.W = lp[i].W; a.C = C; a.G = lp[i].G; a.lines = lp[i].lines;
-        a.img = lp[i].img;
-        a.tma_ok = ((d.nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(lines[i].vel) & 15) == 0);
-        if (slabs) {  // autotuner: scratch wavefield and partial rows, first rows
+        a.C = C; a.G = lp[i].G; a.ncw = ncw; a.extra = extra;
+        if (slabs) {  // autotuner: scratch wavefield and accumulator rows, first rows
             a.slab = (*slabs)[i];
-            a.partials = (*partials)[i];
+            a.acc = reinterpret_cast<unsigned long long*>((*accs)[i]);
             a.z_begin = 0;
             a.z_end = tune_rows(d);
-            a.nz = a.z_end;  // partial rows are indexed by the scratch's depth count
+            a.nz = a.z_end;  // accumulator rows are indexed by the scratch's depth count
         }
         b->line[i].a = a;
         b->line[i].LT = lp[i].LT;
-        b->line[i].P = P[i];
         b->line[i].table = static_cast<const float2*>(lines[i].table);
+        b->line[i].vel = lines[i].vel;
+        b->line[i].norms = reinterpret_cast<double*>(wsb + Lw.norms) + Lw.norm_off[i];
+        b->line[i].head = head;
     }
     b->nitems = b->item_base[n];
     return FXMIG_OK;
 }
 
-static cudaError_t launch_batch_kernel(const BatchArgs& b, size_t smem, int C, int* counter, cudaStream_t s) {
+static cudaError_t launch_batch_kernel(const BatchArgs& b, size_t smem, int C, int warps, int* counter,
+                                       cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    e = ensure_smem(k_migrate_batch, smem, C > 1);
+    e = ensure_smem(k_migrate_batch, smem, false);
     if (e != cudaSuccess) return e;
     const int clusters = std::max(1, std::min(sms_of_device() / C, b.nitems));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(clusters * C);
-    cfg.blockDim = dim3(kBatchWarps * 32);
+    cfg.blockDim = dim3(warps * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -377,67 +433,72 @@ static cudaError_t launch_batch_kernel(const BatchArgs& b, size_t smem, int C, i
     return cudaLaunchKernelEx(&cfg, k_migrate_batch, b);
 }
 
-static cudaError_t expand_tables(int n, const BatchArgs& b, cudaStream_t s) {
-    k_expand_taps_batch<<<dim3(8, std::min(n, 65535)), 256, 0, s>>>(b);
+// Everything the batch kernel reads that depends on the call: the status
+// word, queue counter and per-line heads cleared; tables, slowness fields and
+// zeroed accumulator rows; the image scales of the lines' wavefields.
+static cudaError_t prepare(const BatchArgs& b, unsigned char* wsb, const BatchLayout& Lw, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(wsb, 0, Lw.heads + (size_t)b.nlines * 16, s);
+    if (e != cudaSuccess) return e;
+    k_batch_prep<<<dim3(16, std::min(b.nlines, 65535)), 256, 0, s>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int nwmax = 1;
+    for (int i = 0; i < b.nlines; ++i) nwmax = std::max(nwmax, b.line[i].a.nw);
+    k_batch_norms<<<dim3(nwmax, b.nlines), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const fxmig_line* lines, int n, const fxmig_batch_plan& plan, void* ws, cudaStream_t s) {
     unsigned char* wsb = static_cast<unsigned char*>(ws);
-    std::vector<BatchArgs> hold(1);  // ~23 KB of launch arguments
+    std::vector<BatchArgs> hold(1);  // ~25 KB of launch arguments
     BatchArgs& b = hold[0];
     size_t smem = 0;
-    if (fill_args(lines, n, plan, wsb, &b, &smem, nullptr, nullptr) != FXMIG_OK) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(wsb, 0, sizeof(int), s);
+    int warps = 0;
+    if (fill_args(lines, n, plan, wsb, &b, &smem, &warps, nullptr, nullptr) != FXMIG_OK) return cudaErrorInvalidValue;
+    const BatchLayout Lw = batch_layout(lines, n, false);
+    cudaError_t e = prepare(b, wsb, Lw, s);
     if (e != cudaSuccess) return e;
-    e = expand_tables(n, b, s);
-    if (e != cudaSuccess) return e;
-    return launch_batch_kernel(b, smem, plan.cluster, b.counter, s);
+    return launch_batch_kernel(b, smem, plan.cluster, warps, b.counter, s);
 }
 
 int batch_autotune(const fxmig_line* lines, int n, fxmig_batch_plan* out, void* ws, cudaStream_t s,
                    float* best_ms) {
     unsigned char* wsb = static_cast<unsigned char*>(ws);
-    const std::vector<int> pmax = tune_pmax(lines, n);
-    const BatchLayout Lw = batch_layout(lines, n, pmax.data());
-    // scratch wavefields (copies of the caller's) and partial rows
+    const BatchLayout Lw = batch_layout(lines, n, true);
+    // scratch wavefields (copies of the caller's) and accumulators
     std::vector<float2*> slabs(n);
-    std::vector<float*> parts(n);
+    std::vector<float*> accs(n);
     size_t o = Lw.scratch;
     for (int i = 0; i < n; ++i) {
         const fxmig_desc& d = lines[i].d;
         slabs[i] = reinterpret_cast<float2*>(wsb + o);
         o += r256((size_t)d.nw * d.nx * 8);
-        parts[i] = reinterpret_cast<float*>(wsb + o);
-        o += r256((size_t)pmax[i] * tune_rows(d) * d.nx * 4);
+        accs[i] = reinterpret_cast<float*>(wsb + o);
+        o += r256((size_t)image_planes(d.nx) * tune_rows(d) * d.nx * 4);
     }
     const std::vector<fxmig_batch_plan> cands = tune_candidates(lines, n);
     if (cands.empty()) return FXMIG_EINVAL;
-    cudaError_t e = cudaMemsetAsync(wsb, 0, sizeof(int), s);
-    if (e != cudaSuccess) return FXMIG_ECUDA;
     std::vector<BatchArgs> hold(1);
     BatchArgs& b = hold[0];
-    {  // the expanded tables do not depend on the plan
-        size_t sm0 = 0;
-        if (fill_args(lines, n, cands[0], wsb, &b, &sm0, nullptr, nullptr) != FXMIG_OK) return FXMIG_EINVAL;
-        if (expand_tables(n, b, s) != cudaSuccess) return FXMIG_ECUDA;
-    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FXMIG_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return FXMIG_ECUDA;
     }
+    cudaError_t e = cudaSuccess;
     float best = 1e30f;
     fxmig_batch_plan best_plan = {0, 0};
     for (const fxmig_batch_plan& p : cands) {
         size_t smem = 0;
-        if (fill_args(lines, n, p, wsb, &b, &smem, &slabs, &parts) != FXMIG_OK) continue;
+        int warps = 0;
+        if (fill_args(lines, n, p, wsb, &b, &smem, &warps, &slabs, &accs) != FXMIG_OK) continue;
         for (int i = 0; i < n && e == cudaSuccess; ++i)
             e = cudaMemcpyAsync(slabs[i], lines[i].slab, (size_t)lines[i].d.nw * lines[i].d.nx * 8,
                                 cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = prepare(b, wsb, Lw, s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = launch_batch_kernel(b, smem, p.cluster, b.counter, s);
+        if (e == cudaSuccess) e = launch_batch_kernel(b, smem, p.cluster, warps, b.counter, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -19,8 +19,39 @@ namespace fxmig_impl {
 enum : int {
     kStatusTimeout = 1,   // a bounded mbarrier wait gave up
     kStatusVelocity = 2,  // a velocity sample was not finite and > 0
+    kStatusOverflow = 4,  // an image contribution beyond the fixed-point accumulator's range
 };
-constexpr size_t kStatusBytes = 256;  // status word + padding at the workspace start
+// Workspace head: status word, then the image scale exponent and the
+// counter of the line-norm blocks (image.cu), padded to 256 bytes.
+constexpr size_t kStatusBytes = 256;
+constexpr int kWsScaleExp = 1;   // int index of the image scale exponent e
+constexpr int kWsNormCount = 2;  // int index of the finished line-norm blocks
+
+// ---------------------------------------------------------- image accumulator
+// The depth loops add every image row into a fixed-point accumulator that the
+// caller owns as `partials` (image_planes(nx) planes of [nz][nx] floats): it
+// starts with acc[nz][slow_pitch(nx)] int64 (value = acc * 2^-e[z]; rows padded
+// to a multiple of 8 so that bulk reductions start on 64 bytes), followed by
+// e[nz] int32.  Every frequency's contribution is converted on its own
+// (image_fixed) and the integer sums do not depend on the order of the
+// additions, so the image is deterministic whatever the launch shape.
+inline int slow_pitch(int nx) { return (nx + 7) & ~7; }
+inline int image_planes(int nx) {
+    const long long bytes = 8LL * slow_pitch(nx) + 4;  // per depth row
+    return (int)((bytes + 4LL * nx - 1) / (4LL * nx));
+}
+// Largest |contribution * 2^e| that converts to int32 (below 2^31).
+constexpr float kImageFixedMax = 2147483520.0f;
+// One frequency's contribution v to a pixel in fixed point (rint(v * scale)
+// as a 32-bit integer, widened); sets `over` for values beyond the range.
+__device__ __forceinline__ long long image_fixed(float v, float scale, bool& over) {
+    float t = v * scale;
+    if (!(fabsf(t) < kImageFixedMax)) {
+        over = true;
+        t = 0.f;
+    }
+    return (long long)__float2int_rn(t);
+}
 
 // Largest operator half-length compiled into the extrapolation kernels; other
 // L are rounded up to the next compiled length with zero taps.
@@ -185,21 +216,43 @@ struct MigratePlan {
     int mode;      // FXMIG_MODE_PERSISTENT or FXMIG_MODE_PER_DEPTH
     int precision; // FXMIG_PREC_*
     int LT;        // compiled half-length >= L
-    int cluster;   // persistent: CTAs per frequency group along x
+    int cluster;   // persistent: CTAs per frequency group (1, or a cluster of 2)
     int groups;    // persistent: frequency groups; per-depth: frequency tiles
-    int warps;     // warps per CTA
-    int W;         // persistent: x segment per CTA (multiple of 8)
+    int warps;     // persistent: compute warps; per-depth: warps per CTA
+    int nr;        // persistent: 8-output items per compute lane and depth step (1 or 2)
+    int extra;     // persistent: the launch has cut lines (extra warp per CTA)
     int lines;     // persistent: max lines per group
     size_t smem;   // dynamic shared memory bytes per CTA
-    int img;       // persistent: imaging buffer in shared memory
-    int nparts;    // partial images written
+    int nparts;    // planes of the image accumulator (image_planes(nx))
 };
 
+// slow_pitch(nx) is also the row pitch of the slowness field in the
+// workspace (floats), so every staged row range starts and ends on 16 bytes.
+
 bool desc_valid(const fxmig_desc* d);
+// Records a CUDA error for fxmig_last_error() and returns FXMIG_ECUDA.
+int record_cuda_error(cudaError_t e, const char* where);
 int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* plan);
 size_t migrate_ws_bytes(const fxmig_desc* d);
+// The part of the FXMIG_WS_MIGRATE workspace the persistent form uses (no
+// second wavefield).
+size_t migrate_ws_bytes_persistent(const fxmig_desc* d);
 size_t t2f_ws_bytes(const fxmig_desc* d);
 bool t2f_supported(int nt);
+
+// Plan of the persistent depth loop (depth.cuh) for storage of esize bytes
+// per value; req_*: requested cluster size, groups, compute warps (0 = auto).
+int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int req_w, MigratePlan* p);
+// Per call, before a depth loop: the image scale exponent from the wavefield
+// (written to ws[kWsScaleExp] and to the scale rows [z_begin, z_end) of the
+// accumulator) and zeroed accumulator rows.  norms: nw doubles of scratch;
+// the workspace head (status, exponent, counter) must be zero.
+cudaError_t launch_image_prep(const fxmig_desc* d, const void* slab, float* partials, int z_begin, int z_end,
+                              void* ws, double* norms, cudaStream_t s);
+// Slowness s = fl32(1/v) of rows [z_begin, z_end) into slow[nz][slow_pitch(nx)]
+// (pitch padding repeats the last sample); flags bad velocities.
+cudaError_t launch_slowness(const fxmig_desc* d, const float* vel, float* slow, int z_begin, int z_end,
+                            int* status, cudaStream_t s);
 
 // kvals == nullptr: the nk-entry table grid (n == nk); else n wavenumbers kvals.
 cudaError_t launch_design(const fxmig_desc* d, const double* kvals, int n, void* table, void* table64,
@@ -212,10 +265,10 @@ cudaError_t launch_migrate(const fxmig_desc* d, const MigratePlan& plan, void* s
                            const void* table, float* partials, int z_begin, int z_end, void* ws,
                            cudaStream_t s, bool precompute_slowness);
 // 16-bit storage forms of the persistent kernel (migrate_rp.cu)
-struct MigrateArgs;
+struct DepthArgs;
 bool rp_compiled(int LT);
 cudaError_t expand_taps_rp(int precision, const float2* table, int nk, int L, int LT, void* taps, cudaStream_t s);
-cudaError_t launch_persistent_rp(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s);
+cudaError_t launch_depth_rp(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s);
 // many lines in one persistent launch (batch.cu)
 bool batch_descs_valid(const fxmig_line* lines, int n);
 bool batch_lines_valid(const fxmig_line* lines, int n);

@@ -1,52 +1,126 @@
-// image.cu -- imaging reduction (Algorithm 1, "calculate depth row by summing
-// over frequencies"; Sec. III, second kernel): the depth section is the sum of
-// the partial images written by the depth loop, taken in ascending partial
-// order so that the result does not depend on scheduling.  HBM-bound: reads
-// nparts * nz * nx floats once, writes nz * nx.
+// image.cu -- imaging (Algorithm 1, "calculate depth row by summing over
+// frequencies"; Sec. III, second kernel).
+//
+// The depth loops add every depth row of Re P, frequency by frequency, into a
+// fixed-point accumulator acc[z][x] (int64, value acc * 2^-e).
+// Integer addition is associative, so the image does not depend on the order
+// in which the CTAs add their rows: the result is deterministic for any launch
+// shape, and no partial image per CTA group is written or read back.
+//
+// The scale 2^e comes from a bound on every contribution.  Each step of Eq. 1
+// with the guarded operators (|H| <= 1) does not increase the energy of a
+// frequency line, so the contribution of one frequency to one pixel is
+// |Re P(x, z, w)| <= ||P(., z_begin, w)||_2 <= Bmax = max_w ||P(., z_begin, w)||_2.
+// Every depth loop converts the contribution of each frequency on its own,
+// rint(Re P * 2^e) as a 32-bit integer (the fast float-to-int32 conversion;
+// float-to-int64 runs on the FP64 pipe), and adds it into the int64
+// accumulator.  With Bmax < 2^k and e = 23 - k a contribution stays below 2^31
+// with a growth allowance of 2^8 (laterally varying operators are not exactly
+// norm-bounded); contributions beyond that are reported (FXMIG_ERANGE).  The
+// rounding of a contribution is at most 2^-(e+1) = 2^(k-24) <= Bmax 2^-23, and
+// the sum over nw frequencies of such independent roundings stays near the
+// FP32 rounding of the image itself.
+#include <math.h>
+
 #include "fxmig_internal.cuh"
 
 namespace fxmig_impl {
 
-__global__ void __launch_bounds__(256) k_image_v4(const float4* __restrict__ partials, int nparts, size_t n4,
-                                                   float4* __restrict__ image) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-        float4 acc = __ldcs(partials + i);
-        for (int p = 1; p < nparts; ++p) {
-            const float4 v = __ldcs(partials + (size_t)p * n4 + i);
-            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-        }
-        image[i] = acc;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_image_v1(const float* __restrict__ partials, int nparts, size_t n,
-                                                   float* __restrict__ image) {
+// image[z][x] = acc[z][x] * 2^-e[z]  (HBM-bound: 12 bytes per pixel)
+__global__ void __launch_bounds__(256) k_image_fixed(const long long* __restrict__ acc, const int* __restrict__ e,
+                                                      int nz, int nx, int pitch, float* __restrict__ image) {
+    const size_t n = (size_t)nz * nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float acc = partials[i];
-        for (int p = 1; p < nparts; ++p) acc += partials[(size_t)p * n + i];
-        image[i] = acc;
+        const int z = (int)(i / (size_t)nx), x = (int)(i - (size_t)z * nx);
+        image[i] = (float)ldexp((double)__ldcs(acc + (size_t)z * pitch + x), -__ldg(e + z));
     }
 }
 
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image, cudaStream_t s) {
     const size_t n = (size_t)d->nz * d->nx;
     if (n == 0) return cudaSuccess;
+    (void)nparts;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 148;
-    const bool v4 = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(partials) & 15) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(image) & 15) == 0);
-    const size_t items = v4 ? n / 4 : n;
-    size_t blocks = (items + 255) / 256;
+    size_t blocks = (n + 255) / 256;
     const size_t cap = (size_t)sms * 8;
     if (blocks > cap) blocks = cap;
-    if (nparts == 0) return cudaMemsetAsync(image, 0, n * sizeof(float), s);
-    if (v4)
-        k_image_v4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(partials), nparts, n / 4,
-                                                   reinterpret_cast<float4*>(image));
-    else
-        k_image_v1<<<(unsigned)blocks, 256, 0, s>>>(partials, nparts, n, image);
+    const int pitch = slow_pitch(d->nx);
+    const long long* acc = reinterpret_cast<const long long*>(partials);
+    const int* e = reinterpret_cast<const int*>(acc + (size_t)d->nz * pitch);
+    k_image_fixed<<<(unsigned)blocks, 256, 0, s>>>(acc, e, d->nz, d->nx, pitch, image);
+    return cudaGetLastError();
+}
+
+// Block b: ||P(., b)||_2 of frequency line b (FP64, fixed summation order).
+// The last block to finish takes the largest norm, picks e, writes it to the
+// workspace and to the scale rows [z_begin, z_end), and re-arms the counter.
+// A call that continues a depth range (z_begin > 0) keeps the exponent of row
+// z_begin - 1 when it lies within 4 bits of the one the wavefield would get, so
+// that a migration split into consecutive calls gives the same image as one
+// call.  With guarded operators the energy only decreases with depth (the kept
+// exponent is then coarser); learned operators may let it grow a little (the
+// kept exponent is finer, and at most 4 bits of the 2^8 allowance are spent).
+__global__ void __launch_bounds__(256) k_line_norms(const float2* __restrict__ slab, int nx, int nw,
+                                                     double* __restrict__ norms, int* ws_head, int* e_rows,
+                                                     int z_begin, int z_end) {
+    __shared__ double red[256];
+    __shared__ bool last;
+    const float2* p = slab + (size_t)blockIdx.x * nx;
+    double s = 0.0;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const float2 v = p[x];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        norms[blockIdx.x] = sqrt(red[0]);
+        __threadfence();
+        last = atomicAdd(&ws_head[kWsNormCount], 1) == nw - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __shared__ int e_sh;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        double B = 0.0;
+        for (int j = 0; j < nw; ++j) B = fmax(B, *((volatile const double*)(norms + j)));
+        int e = 0;
+        if (B > 0.0 && B <= 1.0e300) {
+            int k;
+            frexp(B, &k);  // Bmax < 2^k
+            e = 23 - k;
+        }
+        e = e < -126 ? -126 : (e > 127 ? 127 : e);
+        if (z_begin > 0) {
+            const int ep = e_rows[z_begin - 1];
+            if (ep >= e - 4 && ep <= e + 4) e = ep;
+        }
+        e_sh = e;
+        ws_head[kWsScaleExp] = e;
+        ws_head[kWsNormCount] = 0;
+    }
+    __syncthreads();
+    for (int z = z_begin + (int)threadIdx.x; z < z_end; z += blockDim.x) e_rows[z] = e_sh;
+}
+
+cudaError_t launch_image_prep(const fxmig_desc* d, const void* slab, float* partials, int z_begin, int z_end,
+                              void* ws, double* norms, cudaStream_t s) {
+    const int pitch = slow_pitch(d->nx);
+    long long* acc = reinterpret_cast<long long*>(partials);
+    cudaError_t e = cudaMemsetAsync(acc + (size_t)z_begin * pitch, 0, (size_t)(z_end - z_begin) * pitch * 8, s);
+    if (e != cudaSuccess) return e;
+    int* head = static_cast<int*>(ws);
+    int* e_rows = reinterpret_cast<int*>(acc + (size_t)d->nz * pitch);
+    k_line_norms<<<d->nw, 256, 0, s>>>(static_cast<const float2*>(slab), d->nx, d->nw, norms, head, e_rows, z_begin,
+                                       z_end);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,8 @@
 // migrate_rp.cu -- the persistent depth loop with 16-bit storage (FP16 or
 // BF16 wavefield lines in shared memory, 16-bit taps with an optional hi/lo
-// split); FP32 arithmetic.  Same kernel as the FP32 form (persistent.cuh),
+// split); FP32 arithmetic.  Same kernel as the FP32 form (depth.cuh),
 // compiled here for LT = 8, 12, 17 so the FP32 translation unit stays small.
-#include "persistent.cuh"
+#include "depth.cuh"
 
 namespace fxmig_impl {
 
@@ -44,18 +44,41 @@ cudaError_t expand_taps_rp(int precision, const float2* table, int nk, int L, in
     }
 }
 
+template <int LT, class WS, class TP>
+static cudaError_t launch_one(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
+    auto kern1 = k_depth<LT, WS, TP, 1, false>;
+    auto kern2 = k_depth<LT, WS, TP, 2, false>;
+    auto kern = plan.nr == 1 ? kern1 : kern2;
+    if (plan.nr != 1 && plan.nr != 2) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem(kern, plan.smem, false);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.groups * plan.cluster);
+    cfg.blockDim = dim3((plan.warps + plan.extra) * 32);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = plan.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <int LT>
-static cudaError_t launch_prec(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
+static cudaError_t launch_prec(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
     switch (plan.precision) {
-        case FXMIG_PREC_FP16: return launch_persistent<LT, WsF16, TapHalf<H2F16, false>>(plan, a, s);
-        case FXMIG_PREC_BF16: return launch_persistent<LT, WsBF16, TapHalf<H2BF16, false>>(plan, a, s);
-        case FXMIG_PREC_FP16_SPLIT: return launch_persistent<LT, WsF16, TapHalf<H2F16, true>>(plan, a, s);
-        case FXMIG_PREC_BF16_SPLIT: return launch_persistent<LT, WsBF16, TapHalf<H2BF16, true>>(plan, a, s);
+        case FXMIG_PREC_FP16: return launch_one<LT, WsF16, TapHalf<H2F16, false>>(plan, a, s);
+        case FXMIG_PREC_BF16: return launch_one<LT, WsBF16, TapHalf<H2BF16, false>>(plan, a, s);
+        case FXMIG_PREC_FP16_SPLIT: return launch_one<LT, WsF16, TapHalf<H2F16, true>>(plan, a, s);
+        case FXMIG_PREC_BF16_SPLIT: return launch_one<LT, WsBF16, TapHalf<H2BF16, true>>(plan, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_persistent_rp(const MigratePlan& plan, const MigrateArgs& a, cudaStream_t s) {
+cudaError_t launch_depth_rp(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
     switch (plan.LT) {
         case 8: return launch_prec<8>(plan, a, s);
         case 12: return launch_prec<12>(plan, a, s);

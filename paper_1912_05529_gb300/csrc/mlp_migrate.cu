@@ -10,20 +10,21 @@
 //                   of nw * count);
 //   per block of Zc rows: the network writes the operators of all pairs of
 //   the block (k_mlp_infer_tc), then the block's depth steps run in the
-//   persistent form (the frequency lines stay in shared memory for the
-//   block's rows; the staged rows hold every point's pair index instead of
-//   its slowness), or, when rows cannot be staged by TMA (nx not a multiple
-//   of 4), one Eq. 1 launch per row streams the wavefield through L2/HBM
-//   (k_step_pairs, 256 outputs of a frequency tile per CTA, output x of
-//   line w using the operator of pair (w, uidx[z][x])).
+//   persistent form (depth.cuh: the frequency lines stay in shared memory for
+//   the block's rows; the staged rows hold every point's pair index instead
+//   of its slowness), or, for lines too wide for it, one Eq. 1 launch per row
+//   streams the wavefield through L2/HBM (k_step_pairs, 256 outputs of a
+//   frequency tile per CTA, output x of line w using the operator of pair
+//   (w, uidx[z][x])).
+// Image rows go into the fixed-point accumulator of image.cu.
 // Every launch reads its counts from device memory: no host synchronisation.
 #include <float.h>
 
 #include <algorithm>
 
+#include "depth.cuh"
 #include "fir.cuh"
 #include "mlp_internal.cuh"
-#include "persistent.cuh"
 
 namespace fxmig_impl {
 
@@ -32,8 +33,10 @@ constexpr int kUniqueThreads = 1024;
 // Distinct slowness values of velocity row z_begin + blockIdx.x.  Keys are the
 // bit patterns of s = fl32(1/v) (s > 0 for valid velocities, so bit order is
 // value order); padding keys 0xffffffff sort last.
+// uidx rows have pitch `pitch` (slow_pitch(nx)); the padding repeats the
+// row's last index, like the slowness field's.
 __global__ void __launch_bounds__(kUniqueThreads) k_row_unique(const float* __restrict__ vel, int nx, int nxp,
-                                                               int z_begin, float* __restrict__ uval,
+                                                               int pitch, int z_begin, float* __restrict__ uval,
                                                                int* __restrict__ uidx, int* __restrict__ cnt,
                                                                int* status) {
     extern __shared__ uint32_t keys[];      // [nxp]
@@ -108,14 +111,14 @@ __global__ void __launch_bounds__(kUniqueThreads) k_row_unique(const float* __re
     if (tid == 0) cnt[z] = count;
     __syncthreads();
     // index of every point's value (exact match by binary search)
-    for (int x = tid; x < nx; x += nth) {
-        const uint32_t key = __float_as_uint(__frcp_rn(v[x]));
+    for (int x = tid; x < pitch; x += nth) {
+        const uint32_t key = __float_as_uint(__frcp_rn(v[x < nx ? x : nx - 1]));
         int lo = 0, hi = count - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (uniq[mid] < key) lo = mid + 1; else hi = mid;
         }
-        uidx[(size_t)z * nx + x] = lo;
+        uidx[(size_t)z * pitch + x] = lo;
     }
 }
 
@@ -135,14 +138,16 @@ constexpr int kPairWarps = 8;
 constexpr int kPairTile = 256;  // x outputs per CTA (32 lanes x 8)
 
 struct PairStepArgs {
-    int nx, nz, nw, G, z, z0;
+    int nx, nz, nw, G, z, z0, pitch;
     const float2* in;
     float2* out;
-    const int* uidx;         // [nz][nx]
-    const int* cnt;          // [nz]
-    const long long* base;   // [nz+1]
-    const float4* taps;      // operators of the block starting at row z0
-    float* partials;         // [G][nz][nx]
+    const int* uidx;           // [nz][pitch]
+    const int* cnt;            // [nz]
+    const long long* base;     // [nz+1]
+    const float4* taps;        // operators of the block starting at row z0
+    unsigned long long* acc;   // [nz][nx] image accumulator
+    const int* scale_exp;
+    int* status;
 };
 
 template <int LT>
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_step_pairs(const PairStepAr
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int SP = ((kPairTile + 2 * LT + 7) >> 3) * 10;
     int* urow = reinterpret_cast<int*>(smem);                                   // [256]
-    float* imgw = reinterpret_cast<float*>(urow + kPairTile);                   // [warps][256]
+    long long* imgw = reinterpret_cast<long long*>(urow + kPairTile);           // [warps][256]
     float2* buf = reinterpret_cast<float2*>(imgw + kPairWarps * kPairTile);     // [warps][SP]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * kPairTile;
@@ -159,12 +164,15 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_step_pairs(const PairStepAr
     const int z = a.z;
     {
         const int x = x0 + tid;
-        urow[tid] = x < a.nx ? a.uidx[(size_t)z * a.nx + x] : 0;
+        urow[tid] = x < a.nx ? a.uidx[(size_t)z * a.pitch + x] : 0;
     }
     __syncthreads();
     const int c = a.cnt[z];
     const float4* row_taps = a.taps + (size_t)(a.base[z] - a.base[a.z0]) * (LT + 1);
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // image: every frequency's contribution in fixed point, summed exactly
+    long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float scale = depth_scale(*a.scale_exp);
+    bool over = false;
     float2* wb = buf + (size_t)warp * SP;
     int u8[8];
 #pragma unroll
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_step_pairs(const PairStepAr
         u64 res[8];
         fir8_ptrs<LT>(wb + lane * 10, tp, res, re);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) acc[r] += re[r];
+        for (int r = 0; r < 8; ++r) acc[r] += image_fixed(re[r], scale, over);
         float2* dst = a.out + (size_t)l * a.nx;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -193,15 +201,16 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_step_pairs(const PairStepAr
         }
         __syncwarp();
     }
+    if (over) atomicOr(a.status, kStatusOverflow);
 #pragma unroll
     for (int r = 0; r < 8; ++r) imgw[warp * kPairTile + lane * 8 + r] = acc[r];
     __syncthreads();
     {
         const int x = x0 + tid;
         if (x < a.nx) {
-            float s = 0.f;
+            long long s = 0;
             for (int w = 0; w < kPairWarps; ++w) s += imgw[w * kPairTile + tid];
-            a.partials[((size_t)blockIdx.y * a.nz + z) * a.nx + x] = s;
+            if (s) depth_red_add_u64(a.acc + (size_t)z * a.pitch + x, s);
         }
     }
 }
@@ -218,15 +227,11 @@ int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p) {
     const int LT = compiled_half_length(d->L);
     if (LT < 0) return FXMIG_EINVAL;
     p->LT = LT;
-    // persistent form when pair-index rows can be staged by TMA
-    p->persistent = 0;
-    if ((d->nx & 3) == 0) {
-        fxmig_launch lp = {};
-        lp.mode = FXMIG_MODE_PERSISTENT;
-        if (plan_migrate(d, &lp, &p->pplan) == FXMIG_OK) p->persistent = 1;
-    }
+    // persistent form (pair-index rows staged like slowness rows) when the
+    // lines can be planned; one launch per row otherwise
+    p->persistent = plan_depth(d, LT, 8, 0, 0, 0, &p->pplan) == FXMIG_OK ? 1 : 0;
     p->groups = p->persistent ? p->pplan.groups : std::max(1, std::min(d->nw, 16));
-    p->nparts = p->persistent ? p->pplan.nparts : p->groups;
+    p->nparts = image_planes(d->nx);
     // rows per operator block: worst-case operator storage (every point of a
     // row distinct) of about 2 GiB at most
     const double row_bytes = (double)d->nw * d->nx * (LT + 1) * 16.0;
@@ -236,11 +241,12 @@ int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p) {
 
 namespace {
 struct MlpWs {
-    int* status;
+    int* head;
     int* uidx;
     float* uval;
     int* cnt;
     long long* base;
+    double* norms;
     float4* taps;
     float2* slab2;
     size_t total;
@@ -250,16 +256,17 @@ MlpWs mlp_ws_layout(const fxmig_desc* d, const MlpMigratePlan& p, void* ws) {
     unsigned char* b = static_cast<unsigned char*>(ws);
     MlpWs w;
     size_t o = kStatusBytes;
-    w.status = reinterpret_cast<int*>(b);
-    const size_t plane = (size_t)d->nz * d->nx * 4;
+    w.head = reinterpret_cast<int*>(b);
     w.uidx = reinterpret_cast<int*>(b + o);
-    o += r256(plane);
+    o += r256((size_t)d->nz * slow_pitch(d->nx) * 4);
     w.uval = reinterpret_cast<float*>(b + o);
-    o += r256(plane);
+    o += r256((size_t)d->nz * d->nx * 4);
     w.cnt = reinterpret_cast<int*>(b + o);
     o += r256((size_t)d->nz * 4);
     w.base = reinterpret_cast<long long*>(b + o);
     o += r256((size_t)(d->nz + 1) * 8);
+    w.norms = reinterpret_cast<double*>(b + o);
+    o += r256((size_t)d->nw * 8);
     w.taps = reinterpret_cast<float4*>(b + o);
     o += r256((size_t)p.zc * d->nw * d->nx * (p.LT + 1) * 16);
     w.slab2 = reinterpret_cast<float2*>(b + o);
@@ -276,10 +283,9 @@ size_t mlp_migrate_ws_bytes(const fxmig_desc* d) {
 }
 
 template <int LT>
-static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& plan, const MlpWs& w,
-                                     PairStepArgs a, int z0, int z1, float2* bufs[2], int& parity,
-                                     cudaStream_t s) {
-    const size_t smem = (size_t)(kPairTile + kPairWarps * kPairTile) * 4 +
+static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& plan, PairStepArgs a, int z0,
+                                     int z1, float2* bufs[2], int& parity, cudaStream_t s) {
+    const size_t smem = (size_t)kPairTile * 4 + (size_t)kPairWarps * kPairTile * 8 +
                         (size_t)kPairWarps * (((kPairTile + 2 * LT + 7) >> 3) * 10) * 8;
     cudaError_t e = ensure_smem(k_step_pairs<LT>, smem);
     if (e != cudaSuccess) return e;
@@ -297,57 +303,75 @@ static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& 
     return cudaSuccess;
 }
 
-// One pair-mode persistent launch, with CTA-scope halo waits when the
-// halos arrive by bulk copies only (halo_bulk_only).
 template <int LT>
-static cudaError_t launch_pairs(const MigratePlan& pp, const MigrateArgs& pa, cudaStream_t s) {
-    if (halo_bulk_only<LT>(pp.W, pp.cluster, pp.lines, 8))
-        return launch_persistent<LT, WsF32, TapF32, true, true>(pp, pa, s);
-    return launch_persistent<LT, WsF32, TapF32, true>(pp, pa, s);
+static cudaError_t launch_pairs(const MigratePlan& pp, const DepthArgs& pa, cudaStream_t s) {
+    auto kern1 = k_depth<LT, WsF32, TapF32, 1, true>;
+    auto kern2 = k_depth<LT, WsF32, TapF32, 2, true>;
+    auto kern = pp.nr == 1 ? kern1 : kern2;
+    cudaError_t e = ensure_smem(kern, pp.smem, false);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pp.groups * pp.cluster);
+    cfg.blockDim = dim3((pp.warps + pp.extra) * 32);
+    cfg.dynamicSmemBytes = pp.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = pp.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, pa);
 }
 
 cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, void* slab, const float* vel,
                                const float* params, float* partials, int z_begin, int z_end, void* ws,
                                cudaStream_t s) {
     const MlpWs w = mlp_ws_layout(d, plan, ws);
-    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(w.head, 0, 16, s);
     if (e != cudaSuccess || z_begin == z_end) return e;
-    const int nxp = next_pow2(d->nx);
-    const int nth = std::min(kUniqueThreads, nxp);
-    const size_t usmem = (size_t)nxp * 8;
+    const int nxs = next_pow2(d->nx);
+    const int pitch = slow_pitch(d->nx);
+    const int nth = std::min(kUniqueThreads, nxs);
+    const size_t usmem = (size_t)nxs * 8;
     e = ensure_smem(k_row_unique, usmem);
     if (e != cudaSuccess) return e;
-    k_row_unique<<<z_end - z_begin, nth, usmem, s>>>(vel, d->nx, nxp, z_begin, w.uval, w.uidx, w.cnt, w.status);
+    k_row_unique<<<z_end - z_begin, nth, usmem, s>>>(vel, d->nx, nxs, pitch, z_begin, w.uval, w.uidx, w.cnt,
+                                                     w.head);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_pair_offsets<<<1, 32, 0, s>>>(w.cnt, d->nw, z_begin, z_end, w.base);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_image_prep(d, slab, partials, z_begin, z_end, ws, w.norms, s);
     if (e != cudaSuccess) return e;
     PairStepArgs a = {};
     a.nx = d->nx;
     a.nz = d->nz;
     a.nw = d->nw;
     a.G = plan.groups;
+    a.pitch = pitch;
     a.uidx = w.uidx;
     a.cnt = w.cnt;
     a.base = w.base;
     a.taps = w.taps;
-    a.partials = partials;
+    a.acc = reinterpret_cast<unsigned long long*>(partials);
+    a.scale_exp = w.head + kWsScaleExp;
+    a.status = w.head;
     float2* bufs[2] = {static_cast<float2*>(slab), w.slab2};
     int parity = 0;
-    MigrateArgs pa = {};
+    DepthArgs pa = {};
     if (plan.persistent) {
-        pa.nx = d->nx; pa.nz = d->nz; pa.nw = d->nw; pa.nk = d->nk; pa.i0 = d->i0; pa.nt = d->nt; pa.L = d->L;
-        pa.dt = d->dt;
+        pa.nx = d->nx; pa.nxp = pitch; pa.nz = d->nz; pa.nw = d->nw; pa.nk = d->nk; pa.L = d->L;
+        pa.i0 = d->i0; pa.nt = d->nt; pa.dt = d->dt;
         pa.slab = static_cast<float2*>(slab);
-        pa.vel = vel;
         pa.slow = reinterpret_cast<const float*>(w.uidx);  // pair indices, staged like slowness rows
         pa.taps = w.taps;
-        pa.partials = partials;
-        pa.status = w.status;
-        pa.W = plan.pplan.W; pa.C = plan.pplan.cluster; pa.G = plan.pplan.groups; pa.lines = plan.pplan.lines;
-        pa.img = plan.pplan.img;
-        pa.tma_ok = 1;  // nx % 4 == 0 and the workspace arrays are 256-byte aligned
+        pa.acc = reinterpret_cast<unsigned long long*>(partials);
+        pa.scale_exp = w.head + kWsScaleExp;
+        pa.status = w.head;
+        pa.C = plan.pplan.cluster; pa.G = plan.pplan.groups; pa.ncw = plan.pplan.warps; pa.extra = plan.pplan.extra;
         pa.pair_cnt = w.cnt;
         pa.pair_base = w.base;
     }
@@ -370,10 +394,10 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
             continue;
         }
         switch (plan.LT) {
-            case 4: e = launch_pair_steps<4>(d, plan, w, a, z0, z1, bufs, parity, s); break;
-            case 8: e = launch_pair_steps<8>(d, plan, w, a, z0, z1, bufs, parity, s); break;
-            case 12: e = launch_pair_steps<12>(d, plan, w, a, z0, z1, bufs, parity, s); break;
-            case 16: e = launch_pair_steps<16>(d, plan, w, a, z0, z1, bufs, parity, s); break;
+            case 4: e = launch_pair_steps<4>(d, plan, a, z0, z1, bufs, parity, s); break;
+            case 8: e = launch_pair_steps<8>(d, plan, a, z0, z1, bufs, parity, s); break;
+            case 12: e = launch_pair_steps<12>(d, plan, a, z0, z1, bufs, parity, s); break;
+            case 16: e = launch_pair_steps<16>(d, plan, a, z0, z1, bufs, parity, s); break;
             default: e = cudaErrorInvalidValue; break;
         }
         if (e != cudaSuccess) return e;

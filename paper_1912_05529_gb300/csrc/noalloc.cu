@@ -6,18 +6,20 @@
 // device, plug-ins that are given buffers but no allocator, and real-time
 // paths that must not call cudaMalloc because it can synchronise the device.
 // They cannot provide the scratch workspace fxmig_migrate needs (the status
-// word and the expanded operator table).  This entry point keeps that scratch
-// in a fixed file-scope device array instead: every GPU that loads the
-// library holds it until the process exits.
+// word, the expanded operator table, the slowness field and the wavefield
+// norms of the image scale).  This entry point keeps that scratch in a fixed
+// file-scope device array instead: every GPU that loads the library holds it
+// until the process exits.
 #include <mutex>
 
 #include "fxmig_internal.cuh"
 
 namespace fxmig_impl {
 
-// Fixed scratch: status word (kStatusBytes) + the expanded operator table,
-// nk * (LT + 1) entries of 16 bytes.
-constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;  // 1 MiB
+// Fixed scratch: the persistent form's workspace without its second
+// wavefield (migrate_ws_bytes_persistent): status head, expanded table,
+// slowness field [nz][nx rounded up to 8], frequency norms.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
@@ -26,7 +28,10 @@ std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the symbol name is only a host-side handle).
+// per device (the symbol name is only a host-side handle).  The address is
+// cached for the life of the process: after cudaDeviceReset on a device the
+// cached address is stale, so callers that reset devices must not use this
+// entry point afterwards.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -61,16 +66,16 @@ extern "C" int fxmig_migrate_noalloc(const fxmig_desc* d, void* slab, const floa
     const int rc = plan_migrate(d, &launch, &plan);
     if (rc != FXMIG_OK) return rc;
     if (nparts < plan.nparts) return FXMIG_ENOSPC;
-    // the status word and the expanded table must fit the fixed scratch
-    const size_t taps = (((size_t)d->nk * (plan.LT + 1) * 16 + 15) & ~size_t(15));
-    if (kStatusBytes + taps > kNoAllocScratchBytes) return FXMIG_ENOSPC;
+    // the persistent form's scratch must fit the fixed array
+    if (migrate_ws_bytes_persistent(d) > kNoAllocScratchBytes) return FXMIG_ENOSPC;
     void* ws = nullptr;
     cudaError_t e = scratch_address(&ws);
-    if (e != cudaSuccess) return FXMIG_ECUDA;
+    if (e != cudaSuccess) return record_cuda_error(e, "fxmig_migrate_noalloc");
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (z_begin == z_end) return FXMIG_OK;
-    // launch_migrate clears the status word and rewrites the table region on
-    // every call, so stale contents from an earlier call are never read.
-    e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s, false);
-    return e == cudaSuccess ? FXMIG_OK : FXMIG_ECUDA;
+    // launch_migrate clears the status head and rewrites the table, slowness
+    // and norms regions on every call, so stale contents from an earlier call
+    // are never read.
+    e = launch_migrate(d, plan, slab, vel, table, partials, z_begin, z_end, ws, s, true);
+    return e == cudaSuccess ? FXMIG_OK : record_cuda_error(e, "fxmig_migrate_noalloc");
 }

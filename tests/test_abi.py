@@ -140,14 +140,29 @@ def test_precision_choices(fx):
 
 
 def test_large_problem_plans_several_waves(fx):
-    # 8192 traces x 601 frequencies do not fit one wave of CTAs in shared
-    # memory: the plan takes more frequency groups; 16-bit storage needs fewer
+    # 8192 traces x 601 frequencies: half a line per CTA (clusters of 2, one
+    # frequency per group, two items per lane), several waves of CTAs
     d = fx.desc_for(nx=8192, nz=2000, nt=4000, dx=6.25, dz=4.0, dt=0.002, f_lo=5.0, f_hi=80.0, L=17,
                     v_min=750.0)
     assert d.nw == 601
-    n32 = fx.fxmig_num_partials(d, fx.Launch(cluster=8))
-    n16 = fx.fxmig_num_partials(d, fx.Launch(cluster=8, precision=fx.FXMIG_PREC_FP16))
-    assert n32 * 8 > 152 and n16 < n32
+    for prec in (fx.FXMIG_PREC_FP32, fx.FXMIG_PREC_FP16):
+        s = fx.fxmig_launch_shape(d, fx.Launch(precision=prec))
+        assert s.cluster == 2 and s.groups == 601 and s.items_per_lane == 2 and s.waves > 1
+        assert s.smem_bytes <= 227 * 1024
+    assert fx.fxmig_num_partials(d) == 3
+
+
+def test_bench_workload_shape(fx):
+    # 2048 traces x 221 frequencies: 76 clusters of 2 over 152 SMs, groups of
+    # 2 or 3 lines laid end to end and cut in half (one cut line per CTA), one
+    # item per compute lane
+    d = fx.desc_for(nx=2048, nz=800, nt=2000, dx=12.5, dz=5.0, dt=0.002, f_lo=5.0, f_hi=60.0, L=12,
+                    v_min=750.0)
+    s = fx.fxmig_launch_shape(d)
+    assert (s.cluster, s.items_per_lane, s.warps) == (2, 1, 12)
+    assert 2 * s.groups >= 140 and s.waves == 1
+    pd = fx.fxmig_launch_shape(d, fx.Launch(mode=fx.FXMIG_MODE_PER_DEPTH))
+    assert pd.mode == fx.FXMIG_MODE_PER_DEPTH and pd.ctas == 8 * pd.groups
 
 
 def test_learned_operator_entry_points_reject_bad_arguments(fx):

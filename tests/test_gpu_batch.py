@@ -82,7 +82,9 @@ class _Batch:
         return [(b["slab"].cpu().numpy(), b["image"].cpu().numpy()) for b in self.bufs]
 
 
-@pytest.mark.parametrize("cluster,cap", [(1, 0), (2, 0), (2, 2), (4, 0), (8, 0)])
+# cluster sizes 1 and 2; caps of 1 (every line of a cluster-2 group cut in
+# half), 2 (no cut) and 3 (the middle line cut)
+@pytest.mark.parametrize("cluster,cap", [(1, 0), (2, 0), (2, 1), (2, 2), (2, 3), (1, 3)])
 def test_batch_matches_oracle_and_is_deterministic(fx, batch_case, cluster, cap):
     plan = fx.BatchPlan(cluster=cluster, lines_cap=cap)
     bt = _Batch(fx, batch_case, plan)

@@ -67,8 +67,9 @@ def _guarded_migrate(fx, w, pr, launch):
     return slab.t.cpu().numpy(), image.t.cpu().numpy()
 
 
-LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=4, warps=7),
-            dict(mode=1, precision=1), dict(mode=1, cluster=2, precision=4), dict(mode=2)]
+LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=2, groups=19),
+            dict(mode=1, cluster=2, groups=56, warps=1), dict(mode=1, precision=1),
+            dict(mode=1, cluster=2, groups=19, precision=4), dict(mode=2)]
 
 
 @pytest.mark.parametrize("nx,L", [(8, 4), (13, 8), (24, 12), (40, 12), (64, 17), (100, 12)])
@@ -119,5 +120,7 @@ def test_batch_and_learned_canaries(fx):
     ws_bytes = fx.fxmig_workspace_bytes(d, fx.FXMIG_WS_MLP_MIGRATE)
     ws = Guarded(ws_bytes, torch.uint8, (ws_bytes,))
     fx.fxmig_mlp_migrate(d, slab.t, torch.from_numpy(pr["vm"]).cuda(), params, parts.t, 0, d.nz, ws.t)
-    assert fx.fxmig_check(ws.t) == fx.FXMIG_OK
+    # an untrained network's operators are far from |H| <= 1: the wavefield may
+    # grow beyond the image accumulator's range, which is reported, not hidden
+    assert fx.fxmig_check(ws.t) in (fx.FXMIG_OK, fx.FXMIG_ERANGE)
     assert slab.intact() and parts.intact() and ws.intact()

@@ -81,9 +81,14 @@ def test_t2f_matches_oracle_dft(fx, nx, nt, i0, nw):
     assert rel_l2(slab.cpu().numpy(), ref) < TOL_T2F * math.log2(nt)
 
 
-LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=4),
-            dict(mode=1, cluster=2, groups=7, warps=5), dict(mode=1, cluster=1, groups=200),
-            dict(mode=2), dict(mode=2, groups=3)]
+# Persistent launches: automatic; one CTA per group; clusters of 2 with 2
+# lines per group (no cut line), with 3 lines per group (the middle line cut
+# between the two CTAs: halo one step behind, redundant outputs), with 7-8
+# lines and two items per compute lane, and with one line per group (every
+# line cut in half, two waves of CTAs); per-depth launches.
+LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=2, groups=37),
+            dict(mode=1, cluster=2, groups=15, warps=6), dict(mode=1, cluster=2, groups=112),
+            dict(mode=1, cluster=1, groups=200), dict(mode=2), dict(mode=2, groups=3)]
 
 
 @pytest.fixture(scope="module")
@@ -161,8 +166,8 @@ def test_diffractor_end_to_end(fx):
 
 
 @pytest.mark.parametrize("nx", [333, 514, 1021])
-@pytest.mark.parametrize("launch", [None, dict(mode=1, cluster=2), dict(mode=1, cluster=4, precision=3),
-                                    dict(mode=2)])
+@pytest.mark.parametrize("launch", [None, dict(mode=1, cluster=2, groups=37),
+                                    dict(mode=1, cluster=2, groups=37, precision=3), dict(mode=2)])
 def test_migrate_widths_not_multiple_of_four(fx, nx, launch):
     # rows of nx % 4 != 0 floats are not 16-byte aligned in device memory:
     # the persistent form then converts velocity rows in shared memory
@@ -182,18 +187,19 @@ def test_migrate_widths_not_multiple_of_four(fx, nx, launch):
 
 @pytest.mark.parametrize("L,prec", [(8, "FP32"), (12, "FP32"), (17, "FP32"), (20, "FP32"),
                                     (12, "FP16_SPLIT"), (17, "FP16_SPLIT")])
-def test_halo_strips(fx, L, prec):
-    # 1000 traces over clusters of 4: segments of 256 traces (the last one
-    # partly beyond the line end), whose edge warps send each line's halo
-    # strip as one piece: a bulk copy of its 16-byte aligned middle and
-    # single stores for the slots around it (odd L; 4-byte values)
+def test_cut_lines(fx, L, prec):
+    # 1000 traces, groups of about 3 lines over clusters of 2: the middle line
+    # of a group is cut between the two CTAs (at chunk 62 of 125, so the cut
+    # falls inside a warp's items), whose extra warps exchange the halo one
+    # step behind and compute the L redundant outputs on the other side; odd
+    # L, 16-bit storage, several depth ranges
     w = small_layered(nx=1000, nz=24, L=L, seed=11, name="layered_1000")
     v, refl, sec = layered_inputs(w)
     pr = problem(w, v, sec)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
-    launch = fx.Launch(mode=1, cluster=4, precision=getattr(fx, "FXMIG_PREC_" + prec))
+    launch = fx.Launch(mode=1, cluster=2, groups=w.nw // 3, precision=getattr(fx, "FXMIG_PREC_" + prec))
     slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch, [0, 9, w.nz])
     P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
     tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if prec == "FP32" else (1e-2, 1e-2)
@@ -201,28 +207,25 @@ def test_halo_strips(fx, L, prec):
     assert rel_l2(image, img_ref) < tol_i
 
 
-@pytest.mark.parametrize("nx", [192, 320, 1000])
+@pytest.mark.parametrize("nx", [16, 40, 192])
 @pytest.mark.parametrize("L,prec", [(4, "FP32"), (12, "FP32"), (17, "FP32"), (20, "FP32"),
                                     (12, "FP16_SPLIT"), (17, "FP16_SPLIT")])
-def test_edge_warp_clusters_of_eight(fx, nx, L, prec):
-    # Clusters of 8 CTAs: segments of 3 chunks (192 traces; at L = 17, 20
-    # the left and right edge chunks of a middle segment overlap and every
-    # chunk is an edge chunk), 5 chunks (320 traces; in 16-bit storage the
-    # padded line length breaks the strip alignment, so every halo output
-    # goes by its own st.async) and 16 chunks (1000 traces; the last segment
-    # runs past the line end).  The edge warp of every CTA computes the
-    # outputs next to its neighbours and feeds both sides.
+def test_cut_lines_tiny_halves(fx, nx, L, prec):
+    # One line per group: every line cut in half, halves of 1 chunk (16
+    # traces), 2-3 chunks (40) and 12 chunks (192).  The halo (2L values) and
+    # the redundant outputs (L) reach past the neighbour's half and past the
+    # line ends, where the wavefield is zero.
     w = small_layered(nx=nx, nz=24, L=L, seed=17, name=f"layered_{nx}")
     v, refl, sec = layered_inputs(w)
     pr = problem(w, v, sec)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
-    launch = fx.Launch(mode=1, cluster=8, precision=getattr(fx, "FXMIG_PREC_" + prec))
+    launch = fx.Launch(mode=1, cluster=2, groups=w.nw, precision=getattr(fx, "FXMIG_PREC_" + prec))
     try:
         fx.fxmig_num_partials(d, launch)
     except fx.FxmigError:
-        pytest.skip("no plan for this shape (segment narrower than the operator, or LT not compiled)")
+        pytest.skip("no plan for this shape (LT not compiled for 16-bit storage)")
     slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch, [0, 7, w.nz])
     P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
     tol_s, tol_i = (TOL_SLICE, TOL_IMAGE) if prec == "FP32" else (1e-2, 1e-2)
@@ -230,11 +233,10 @@ def test_edge_warp_clusters_of_eight(fx, nx, L, prec):
     assert rel_l2(image, img_ref) < tol_i
 
 
-def test_halo_strips_straddling_warps(fx):
-    # 496 traces over clusters of 2: segments of 31 chunks (not a multiple
-    # of 32, so the compute items of a line run across warp boundaries and
-    # the line's edge chunks fall at odd lanes); the edge warp still sends
-    # every strip whole
+def test_cut_lines_straddling_warps(fx):
+    # 496 traces (62 chunks, not a multiple of 32) and groups of about 3
+    # lines over clusters of 2: the segments of a CTA run across warp
+    # boundaries and the cut falls at an odd chunk
     w = small_layered(nx=496, nz=20, L=12, seed=13, name="layered_496")
     v, refl, sec = layered_inputs(w)
     pr = problem(w, v, sec)

@@ -41,16 +41,17 @@ def gpu_migrate(fx, d, P0_32, vm, table32, launch):
     return slab.cpu().numpy(), image.cpu().numpy()
 
 
-# Image rel-L2 bounds against the FP64 oracle.  Rounding the wavefield to
-# 16 bits after every step adds a relative error of up to 2^-11 (FP16) or
-# 2^-8 (BF16) per value and step, of random sign, so after n steps the
-# wavefield error grows like sqrt(n) times that; unsplit taps add a systematic
-# error of the same size per step that grows like n.  The hi/lo split makes
-# the tap error negligible (about 2^-22 / 2^-16).
-PREC_BOUNDS = {"FP16_SPLIT": 1e-2, "FP16": 3e-2, "BF16_SPLIT": 5e-2, "BF16": 1e-1}
-# The same over 2000 steps with 35-tap operators (the 512-trace window): the
-# split forms grow like sqrt(n), the unsplit ones like n.
-WINDOW_BOUNDS = {"FP16_SPLIT": 1e-2, "FP16": 1e-1, "BF16_SPLIT": 5e-2, "BF16": 5e-1}
+# The bar of the reduced-precision forms: image rel-L2 <= 1e-2 against the
+# FP64 oracle.  Rounding the wavefield to 16 bits after every step adds a
+# relative error of up to 2^-11 (FP16) or 2^-8 (BF16) per value and step, of
+# random sign, so after n steps the wavefield error grows like sqrt(n) times
+# that; unsplit taps add a systematic error of the same size per step that
+# grows like n.  The hi/lo split makes the tap error negligible (about 2^-22 /
+# 2^-16).  Only FP16 with split taps stays within the bar on every workload
+# (hundreds to thousands of steps); the others are reported above the bar.
+BAR = 1e-2
+PREC_FORMS = ["FP16_SPLIT", "BF16_SPLIT", "FP16", "BF16"]
+MEETS_BAR = {"FP16_SPLIT"}
 
 
 @pytest.fixture(scope="module")
@@ -64,17 +65,29 @@ def layered_case():
     return w, pr, table32, P0_32, P, img
 
 
-@pytest.mark.parametrize("name", list(PREC_BOUNDS))
-@pytest.mark.parametrize("cluster", [1, 2])
-def test_16bit_forms_against_oracle(fx, layered_case, name, cluster):
+@pytest.fixture(scope="module")
+def split_error(fx, layered_case):
+    w, pr, table32, P0_32, P_ref, img_ref = layered_case
+    d = desc_of(fx, w, pr["k_max"])
+    _, img = gpu_migrate(fx, d, P0_32, pr["vm"], table32, fx.Launch(mode=1, precision=fx.FXMIG_PREC_FP16_SPLIT))
+    return rel_l2(img, img_ref)
+
+
+@pytest.mark.parametrize("name", PREC_FORMS)
+@pytest.mark.parametrize("launch", [dict(cluster=1), dict(cluster=2), dict(cluster=2, groups=37)])
+def test_16bit_forms_against_oracle(fx, layered_case, split_error, name, launch):
     w, pr, table32, P0_32, P_ref, img_ref = layered_case
     d = desc_of(fx, w, pr["k_max"])
     prec = getattr(fx, "FXMIG_PREC_" + name)
-    P, img = gpu_migrate(fx, d, P0_32, pr["vm"], table32, fx.Launch(mode=1, cluster=cluster, precision=prec))
+    P, img = gpu_migrate(fx, d, P0_32, pr["vm"], table32, fx.Launch(mode=1, precision=prec, **launch))
     e_img, e_slab = rel_l2(img, img_ref), rel_l2(P, P_ref)
-    print(f"{name} cluster {cluster}: image rel-L2 {e_img:.3e}, final slice rel-L2 {e_slab:.3e}")
+    print(f"{name} {launch}: image rel-L2 {e_img:.3e}, final slice rel-L2 {e_slab:.3e}")
     assert np.all(np.isfinite(img))
-    assert e_img <= PREC_BOUNDS[name]
+    if name in MEETS_BAR:
+        assert e_img <= BAR
+    else:
+        # above the bar: no accuracy claim beyond the ordering of the forms
+        assert e_img >= split_error
 
 
 def test_split_taps_do_not_lose_accuracy(fx, layered_case):
@@ -89,14 +102,14 @@ def test_split_taps_do_not_lose_accuracy(fx, layered_case):
 
 
 def test_multiwave_plan_matches_oracle(fx, oracle_mod):
-    # 4096 traces x 401 frequencies with clusters of 8 need more CTAs than SMs
+    # 4096 traces x 401 frequencies, one line per cluster of 2 (half a line,
+    # 256 chunks, per CTA): more CTAs than SMs, several waves
     w = W.Workload("wide", nx=4096, dx=12.5, nt=2000, dt=0.002, nz=6, dz=5.0, f_lo=5.0, f_hi=105.0, L=12, seed=9)
     v, refl, sec = layered_inputs(w)
     pr = problem(w, v, sec)
     d = desc_of(fx, w, pr["k_max"])
-    launch = fx.Launch(mode=1, cluster=8)
-    nparts = fx.fxmig_num_partials(d, launch)
-    assert nparts * 8 > torch.cuda.get_device_properties(0).multi_processor_count
+    launch = fx.Launch(mode=1, cluster=2, groups=d.nw)
+    assert fx.fxmig_launch_shape(d, launch).waves > 1
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     P, img = gpu_migrate(fx, d, P0_32, pr["vm"], table32, launch)
@@ -122,7 +135,7 @@ def large_window():
     return ww, pr, table32, P0_32, P, img
 
 
-@pytest.mark.parametrize("name", ["FP32"] + list(PREC_BOUNDS))
+@pytest.mark.parametrize("name", ["FP32"] + PREC_FORMS)
 def test_large_line_window_against_oracle(fx, large_window, name):
     ww, pr, table32, P0_32, P_ref, img_ref = large_window
     assert ww.nw == 601 and ww.L == 17
@@ -131,7 +144,8 @@ def test_large_line_window_against_oracle(fx, large_window, name):
     P, img = gpu_migrate(fx, d, P0_32, pr["vm"], table32, fx.Launch(mode=1, precision=prec))
     e_img, e_slab = rel_l2(img, img_ref), rel_l2(P, P_ref)
     print(f"512-trace window, {name}: image rel-L2 {e_img:.3e}, final slice rel-L2 {e_slab:.3e}")
+    assert np.all(np.isfinite(img))
     if name == "FP32":
         assert e_img < TOL_IMAGE
-    else:
-        assert e_img <= WINDOW_BOUNDS[name]
+    elif name in MEETS_BAR:
+        assert e_img <= BAR
