@@ -290,7 +290,7 @@ def measure_precision(fx, d, b, slab0, steps, flush, launch, prec):
     mean CUDA-event time of fxmig_migrate_ex + fxmig_image, and its image."""
     import torch
     lc = fx.Launch(mode=fx.FXMIG_MODE_PERSISTENT, cluster=launch.cluster, groups=launch.groups,
-                   warps=launch.warps, precision=prec)
+                   warps=launch.warps, precision=prec, ctas_per_sm=launch.ctas_per_sm)
     nparts = fx.fxmig_num_partials(d, lc)
     partials = torch.zeros((nparts, d.nz, d.nx), dtype=torch.float32, device="cuda")
     image = torch.empty((d.nz, d.nx), dtype=torch.float32, device="cuda")
@@ -591,7 +591,8 @@ def run_native(args, w):
     sec, vm = make_inputs(w, seed)
     d = fx.Desc(nx=w.nx, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz, dt=w.dt,
                 theta_max_deg=w.theta_deg, k_max=k_max_of(w, float(vm.min())))
-    launch = fx.Launch(mode=args.mode, cluster=args.cluster, groups=args.groups, warps=args.warps)
+    launch = fx.Launch(mode=args.mode, cluster=args.cluster, groups=args.groups, warps=args.warps,
+                       ctas_per_sm=args.ctas_per_sm)
     b = fx.allocate(d, launch)
     b.section.copy_(torch.from_numpy(sec))
     b.vel.copy_(torch.from_numpy(vm))
@@ -775,6 +776,7 @@ def main(argv=None):
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--groups", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent form: 1, 2, or 0 (auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the learned-operator form")
     ap.add_argument("--train-steps", type=int, default=100000, help="Adam steps of the operator network")

@@ -101,16 +101,19 @@ typedef struct fxmig_desc {
 
 /* Launch choices for fxmig_migrate_ex(); zero-initialised means "choose".
  *   mode           FXMIG_MODE_*
- *   cluster        CTAs sharing one frequency line along x in the persistent
- *                  form (1, 2, 4 or 8), 0 = choose
+ *   cluster        CTAs sharing the frequency lines of a group in the
+ *                  persistent form (1, or a cluster of 2 that may cut one
+ *                  line between its CTAs), 0 = choose
  *   groups         frequency groups (CTA clusters) in the persistent form, or
  *                  frequency tiles in the per-depth form; 0 = choose
  *   warps          compute warps per CTA (persistent form, 1..12), 0 = choose;
- *                  with cluster > 1 one more warp per CTA carries the halo
+ *                  with a cut line one more warp per CTA carries the halo
  *                  exchange between the CTAs of a cluster
- *   precision      FXMIG_PREC_* (persistent form only; 0 = FP32) */
+ *   precision      FXMIG_PREC_* (persistent form only; 0 = FP32)
+ *   ctas_per_sm    persistent form: 1, or 2 (cluster 1, at most 8 compute
+ *                  warps, whole lines; two CTAs share an SM), 0 = choose */
 typedef struct fxmig_launch {
-    int mode, cluster, groups, warps, precision;
+    int mode, cluster, groups, warps, precision, ctas_per_sm;
 } fxmig_launch;
 
 /* Library version (FXMIG_VERSION of the build). */
@@ -145,11 +148,13 @@ int fxmig_num_partials(const fxmig_desc *d, const fxmig_launch *launch);
  *                   group has a line cut between the two CTAs of its cluster)
  *   items_per_lane  8-output items per compute lane and depth step (1 or 2)
  *   waves           ctas over the CTAs the GPU holds at once
+ *   ctas_per_sm     CTAs the persistent kernel is compiled to keep resident
+ *                   on one SM (1 or 2; per-depth form: 0)
  *   smem_bytes      dynamic shared memory per CTA
  * The paper has no counterpart (its launch is one thread per output point).
  * Errors: FXMIG_EINVAL. */
 typedef struct fxmig_shape {
-    int mode, cluster, groups, ctas, warps, items_per_lane, waves;
+    int mode, cluster, groups, ctas, warps, items_per_lane, waves, ctas_per_sm;
     size_t smem_bytes;
 } fxmig_shape;
 int fxmig_launch_shape(const fxmig_desc *d, const fxmig_launch *launch, fxmig_shape *out);

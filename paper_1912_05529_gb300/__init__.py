@@ -80,7 +80,7 @@ class Shape(ctypes.Structure):
     """Mirror of ``fxmig_shape`` (the launch fxmig_migrate_ex makes)."""
     _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
                 ("ctas", ctypes.c_int), ("warps", ctypes.c_int), ("items_per_lane", ctypes.c_int),
-                ("waves", ctypes.c_int), ("smem_bytes", ctypes.c_size_t)]
+                ("waves", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("smem_bytes", ctypes.c_size_t)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -89,7 +89,7 @@ class Shape(ctypes.Structure):
 class Launch(ctypes.Structure):
     """Mirror of ``fxmig_launch`` (zeros = automatic)."""
     _fields_ = [("mode", ctypes.c_int), ("cluster", ctypes.c_int), ("groups", ctypes.c_int),
-                ("warps", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("warps", ctypes.c_int), ("precision", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 def lib():

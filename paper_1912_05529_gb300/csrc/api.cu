@@ -120,12 +120,14 @@ int fxmig_launch_shape(const fxmig_desc* d, const fxmig_launch* launch, fxmig_sh
         out->warps = p.warps;
         out->items_per_lane = 1;
         out->waves = 1;
+        out->ctas_per_sm = 0;
     } else {
         out->ctas = p.groups * p.cluster;
         out->warps = p.warps;
         out->items_per_lane = p.nr;
-        const int resident = p.cluster == 1 ? sms : 2 * (sms / 2);
+        const int resident = p.occ * (p.cluster == 1 ? sms : 2 * (sms / 2));
         out->waves = (out->ctas + resident - 1) / resident;
+        out->ctas_per_sm = p.occ;
     }
     out->smem_bytes = p.smem;
     return FXMIG_OK;

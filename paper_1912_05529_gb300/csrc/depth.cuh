@@ -17,14 +17,14 @@
 //
 // Halo at a cut, one step behind.  The outputs within L of the cut on the
 // other side ("redundant" outputs) are computed by this CTA too, from the
-// neighbour's values one step older: at step t the extra warp pulls the
-// neighbour's time-t values at distance L..2L from the cut (DSMEM loads from
-// the neighbour's outbox, after an mbarrier the neighbour arrives on), and
-// computes the L redundant outputs of time t+1, which the compute warps read
-// at step t+1.  No compute warp ever waits on the neighbour, and the
-// neighbour's values have a whole depth step to arrive.  No data is written
-// into another CTA's shared memory (the only remote operations are mbarrier
-// arrivals and loads), so nothing can land after a CTA has finished.
+// neighbour's values one step older: at the start of step t the extra warp of
+// each CTA pushes its time-t values at distance L..2L from the cut into the
+// other's inbox (remote stores that count their bytes on the receiver's own
+// mbarrier), waits for the neighbour's, and computes the L redundant outputs
+// of time t+1, which the compute warps read at step t+1.  No compute warp
+// ever waits on the neighbour.  Every message is awaited by its receiver
+// before the receiver's next barrier, so none can land after a CTA has
+// finished.
 //
 // Compute warps.  Lane item = 8 consecutive outputs of one segment, the same
 // chunks at every step, so a lane keeps its own 8 values in registers and
@@ -57,6 +57,7 @@ namespace fxmig_impl {
 
 constexpr int kDepthMaxSegs = 8;           // segments per CTA
 constexpr int kDepthRowSlots = 4;          // ring of staged slowness rows
+constexpr int kDepthLaneRowSlots = 3;      // per-lane ring of the decoupled form (rows t, t+1, t+2)
 constexpr int kDepthMaxComputeWarps = 12;  // plus the extra warp of CTAs at a cut
 
 enum : int { kCutLeft = 1, kCutRight = 2 };
@@ -75,7 +76,7 @@ struct DepthLayout {
     int xu0, xu1;               // global x range covered by the segments
     int sx0, rowlen;            // staged slowness range [sx0, sx0 + rowlen) (multiples of 4)
     int buf;                    // elements of one wavefield buffer
-    size_t off_mbar, off_qs, off_box, off_rows, off_img, off_wave, total;
+    size_t off_mbar, off_prog, off_qs, off_box, off_rows, off_img, off_queue, off_wave, total;
     DepthSeg seg[kDepthMaxSegs];
 };
 
@@ -84,10 +85,14 @@ __host__ __device__ inline int depth_ceil8(int v) { return (v + 7) & ~7; }
 // Segments and shared-memory layout of CTA `rank` of group g.  Buffer origin
 // of a segment: P = LT + 8 ceil(LT/8) positions left of x = 0 (so chunk
 // windows start on 8-value blocks and the halo 2L fits), and 2L positions
-// right of its last chunk.  Returns false if the CTA would hold more than
-// kDepthMaxSegs segments or more than one cut.
+// right of its last chunk.  lane_rows: slowness staged per lane (the
+// decoupled form: kDepthLaneRowSlots slots of 8 values per chunk) instead of
+// whole row ranges.  fixq: a queue of the outputs whose operator differs from
+// their item's (8 bytes each, at most 7 per chunk) for the fixup warp.
+// Returns false if the CTA would hold more than kDepthMaxSegs segments or
+// more than one cut.
 __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int C, int g, int rank, int LT,
-                                             int esize, DepthLayout& L) {
+                                             int esize, DepthLayout& L, bool lane_rows = false, bool fixq = false) {
     const int NCL = (nx + 7) >> 3;
     const int lb = (int)(((long long)g * nw) / G), le = (int)(((long long)(g + 1) * nw) / G);
     const long long T = (long long)(le - lb) * NCL;
@@ -138,15 +143,19 @@ __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int
     L.buf = elems;
     size_t o = align16(sizeof(DepthLayout));  // the layout itself heads the CTA's shared memory
     L.off_mbar = o;
-    o += 8 * (kDepthRowSlots + 2);                         // row ring, inbox [parity]
+    o += 8 * (kDepthRowSlots + 3);                         // row ring, inbox [parity], fixup queue
+    L.off_prog = o;
+    o += 4 * kDepthMaxComputeWarps;                        // decoupled form: last step done per warp
     L.off_qs = o;
     o += 4 * kDepthMaxSegs;
     L.off_box = align16(o);
     o = L.off_box + 2 * (size_t)LT * esize;                // outbox [parity][LT]
     L.off_rows = align16(o);
-    o = L.off_rows + (size_t)kDepthRowSlots * L.rowlen * 4;
+    o = L.off_rows + (lane_rows ? (size_t)kDepthLaneRowSlots * L.nchunks * 8 * 4 : (size_t)kDepthRowSlots * L.rowlen * 4);
     L.off_img = align16(o);
     o = L.off_img + 2 * (size_t)L.nchunks * 8 * 8;  // fixed-point image rows [2][chunks][8] int64
+    L.off_queue = align16(o);
+    o = L.off_queue + (fixq ? 16 + (size_t)L.nchunks * 7 * 8 : 0);  // count, entries (position | r, operator)
     L.off_wave = align16(o);
     L.total = L.off_wave + 2 * (size_t)elems * esize;
     return true;
@@ -161,7 +170,7 @@ struct DepthArgs {
     unsigned long long* acc;       // [nz][nx] image accumulator, fixed point 2^e
     const int* scale_exp;          // e, written before the launch
     int* status;
-    int C, G, ncw, extra;          // cluster size, groups, compute warps, extra warp present
+    int C, G, ncw, extra, fixw;    // cluster size, groups, compute warps, extra (halo) warp, fixup warp
     // kPairs: operators per (frequency, distinct slowness) pair
     const int* pair_cnt;           // [nz] distinct values of each row
     const long long* pair_base;    // [nz+1] first pair of each row
@@ -200,20 +209,17 @@ __device__ __forceinline__ u64 depth_stored(u64 v) {
     else return WS::cvt(WS::rnd(v));
 }
 
-// One compute item: the 8 outputs at window base wb (element offset of the
-// chunk's block in the current buffer) from the lane's own 8 values own[]
-// (updated to the outputs) and the 2L halo values of its window.  Outputs at
-// or beyond nv are zero (outside the line).  The 8 outputs use the operator of
-// the first point; returns the mask of outputs whose own operator differs
-// (recomputed by the fixup round), idx1 their common operator (or -1).
-template <int LT, class WS, class TP, bool kPairs>
-__device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
-                                               uint32_t wb, const float* __restrict__ srow, float q, int nk, int nv,
-                                               const typename TP::E* __restrict__ taps, u64 (&own)[8], int& idx1) {
-    constexpr int NWIN = 8 + 2 * LT;
+// Operator analysis of one compute item (8 outputs from slowness values at
+// srow): idx0, the operator of its first point, which all 8 outputs use in
+// the main FIR; the returned mask flags the outputs (r < nv) whose own
+// operator differs (recomputed separately), idx1 their common operator (or
+// -1).  The flagged operators' tap rows are prefetched into L1.
+template <int LT, class TP, bool kPairs>
+__device__ __forceinline__ uint32_t depth_ops(const float* __restrict__ srow, float q, int nk, int nv,
+                                              const typename TP::E* __restrict__ taps, int& idx0, int& idx1) {
     float s8[8];
     load_s8(srow, s8);
-    const int idx0 = depth_op_index<kPairs>(q, s8[0], nk);
+    idx0 = depth_op_index<kPairs>(q, s8[0], nk);
     uint32_t mask = 0;
     idx1 = -1;
     bool same = true;
@@ -234,6 +240,19 @@ __device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict_
         }
         if (uni) idx1 = last;
     }
+    return mask;
+}
+
+// The main FIR of one compute item: the 8 outputs at window base wb (element
+// offset of the chunk's block in the current buffer) with operator idx0, from
+// the lane's own 8 values own[] (updated to the outputs) and the 2L halo
+// values of its window.  Outputs at or beyond nv are zero (outside the line).
+// Outputs flagged in skip are not stored (another warp stores them).
+template <int LT, class WS, class TP>
+__device__ __forceinline__ void depth_fir(const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
+                                          uint32_t wb, int idx0, int nv, const typename TP::E* __restrict__ taps,
+                                          u64 (&own)[8], uint32_t skip) {
+    constexpr int NWIN = 8 + 2 * LT;
     const typename WS::T* wbase = cur + wb;
     u64 w[NWIN];
     // w[LT + r] = own[r]; the 2L halo values come from shared memory in
@@ -282,22 +301,41 @@ __device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict_
         const float2 a = f2_unpack(A[r]), b = f2_unpack(B[r]);
         res[r] = (r < nv) ? f2_pack(a.x - b.y, a.y + b.x) : 0ull;
     }
-    store8<LT, WS>(nxt + wb, res);
+    if (skip == 0u) {
+        store8<LT, WS>(nxt + wb, res);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (!((skip >> r) & 1u)) WS::st1(nxt + wb + phys(r + LT), res[r]);
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) own[r] = depth_stored<WS>(res[r]);
+}
+
+// One compute item with in-warp recomputation of its flagged outputs left to
+// the caller (depth_fixups): depth_ops, then depth_fir storing all 8.
+template <int LT, class WS, class TP, bool kPairs>
+__device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
+                                               uint32_t wb, const float* __restrict__ srow, float q, int nk, int nv,
+                                               const typename TP::E* __restrict__ taps, u64 (&own)[8], int& idx1) {
+    int idx0;
+    const uint32_t mask = depth_ops<LT, TP, kPairs>(srow, q, nk, nv, taps, idx0, idx1);
+    depth_fir<LT, WS, TP>(cur, nxt, wb, idx0, nv, taps, own, 0u);
     return mask;
 }
 
 // The fixed-point image contributions of one item (the real parts of its 8
-// input values; outputs at or beyond nv contribute 0) into the imaging buffer.
+// input values; outputs at or beyond nv contribute 0) into the chunk's 64
+// bytes of the imaging buffer, value pair p at slot p ^ sw (the accumulator's
+// row order, acc_slot; sw = (global chunk >> 1) & 3).
 __device__ __forceinline__ void depth_image_item(long long* __restrict__ dst, const u64 (&own)[8], int nv,
-                                                 float scale, bool& over) {
+                                                 float scale, bool& over, uint32_t sw) {
     long long q[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) q[r] = r < nv ? image_fixed(f2_unpack(own[r]).x, scale, over) : 0;
 #pragma unroll
-    for (int r = 0; r < 8; r += 2)
-        *reinterpret_cast<longlong2*>(dst + r) = make_longlong2(q[r], q[r + 1]);
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<longlong2*>(dst + 2 * (p ^ sw)) = make_longlong2(q[2 * p], q[2 * p + 1]);
 }
 
 // Bulk reduction (add, int64) of `bytes` from this CTA's shared memory into
@@ -370,6 +408,17 @@ __device__ __forceinline__ void depth_fixups(uint32_t mask, uint32_t wb, uint32_
 __device__ __forceinline__ void depth_mbar_arrive_remote(uint32_t remote_bar) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(remote_bar) : "memory");
 }
+// Remote store into another CTA's shared memory whose bytes complete on that
+// CTA's mbarrier (complete_tx): the receiver learns of the data from its own
+// barrier, and nothing of the sender waits for it.
+__device__ __forceinline__ void depth_st_async_b64(uint32_t addr, u64 v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 :: "r"(addr), "l"(v), "r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ void depth_st_async_b32(uint32_t addr, uint32_t v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+                 :: "r"(addr), "r"(v), "r"(remote_bar) : "memory");
+}
 __device__ __forceinline__ u64 depth_ld_cluster_b64(uint32_t addr) {
     u64 v;
     asm volatile("ld.shared::cluster.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
@@ -387,8 +436,20 @@ __device__ __forceinline__ void depth_mbar_inval(uint64_t* bar) {
 // Fixed-point scale 2^e of the image accumulator as a float (e in [-126, 127]).
 __device__ __forceinline__ float depth_scale(int e) { return __int_as_float((e + 127) << 23); }
 
+__device__ __forceinline__ void depth_mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
 // The whole depth loop of group g on the CTAs of one cluster (every CTA of
-// the cluster calls it with the same arguments; blockDim = (ncw + extra) warps).
+// the cluster calls it with the same arguments; blockDim = (ncw + extra +
+// fixw) warps or more).
+//
+// With a fixup warp (fixw), the compute warps do not recompute the outputs
+// whose operator differs from their item's: each lane queues them (position,
+// operator) right after its operator analysis, the warp arrives on the queue
+// barrier, and the fixup warp computes them (single-output FIRs) while the
+// compute warps run their main FIRs, which leave those outputs unwritten.
+// The lanes reload them into their registers after the step barrier.
 template <int LT, class WS, class TP, int NR, bool kPairs>
 __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
@@ -396,17 +457,30 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     const int C = a.C;
     const int rank = C > 1 ? (int)cluster_ctarank() : 0;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    // one item per lane: outputs with a different operator go to the fixup
+    // warp; two items per lane: recomputed in the warp (no room for a queue)
+    constexpr bool kFixW = NR == 1;
+    if (kFixW != (a.fixw != 0)) {  // launch inconsistent with the compiled form (uniform: no barrier reached)
+        if (threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
+        return;
+    }
     const bool compute = warp < a.ncw;
     const bool extra_warp = a.extra && warp == a.ncw;
-    // the thread that stages slowness rows: lane 0 of the extra warp, else thread 0
-    const bool duty = a.extra ? (extra_warp && lane == 0) : tid == 0;
+    const bool fix_warp = kFixW && warp == a.ncw + a.extra;
+    // the thread that stages slowness rows and hands image rows to the
+    // bulk-copy engine: lane 0 of the fixup warp, else of the extra warp,
+    // else thread 0
+    const bool duty = kFixW ? (fix_warp && lane == 0) : a.extra ? (extra_warp && lane == 0) : tid == 0;
 
     DepthLayout& L = *reinterpret_cast<DepthLayout*>(smem);
-    if (tid == 0) depth_layout(a.nx, a.nxp, a.nw, a.G, C, g, rank, LT, WS::kBytes, L);
+    if (tid == 0) depth_layout(a.nx, a.nxp, a.nw, a.G, C, g, rank, LT, WS::kBytes, L, false, kFixW);
     __syncthreads();
     const DepthSeg* segs = L.seg;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_mbar);
     uint64_t* inbar = mbar + kDepthRowSlots;  // [parity]
+    uint64_t* qbar = mbar + kDepthRowSlots + 2;
+    int* qcount = reinterpret_cast<int*>(smem + L.off_queue);
+    uint2* queue = reinterpret_cast<uint2*>(smem + L.off_queue + 16);
     float* qs = reinterpret_cast<float*>(smem + L.off_qs);
     T* box = reinterpret_cast<T*>(smem + L.off_box);
     float* rows = reinterpret_cast<float*>(smem + L.off_rows);
@@ -422,7 +496,9 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     }
     if (tid == 0) {
         for (int b = 0; b < kDepthRowSlots; ++b) mbar_init(&mbar[b], 1);
-        for (int b = 0; b < 2; ++b) mbar_init(&inbar[b], 1);  // one lane of the neighbour's extra warp arrives
+        for (int b = 0; b < 2; ++b) mbar_init(&inbar[b], 1);  // the local expect_tx arrival (plus the bytes)
+        mbar_init(qbar, (uint32_t)a.ncw);                      // every compute warp, once per step
+        if (kFixW) *qcount = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -487,13 +563,13 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
 
     if (compute) {
         // ---- the lane's items (the same chunks at every step)
-        uint32_t wb[NR], ro[NR];
+        uint32_t wb[NR], ro[NR], sw[NR];
         float qv[NR];
         int nv[NR], ln[NR];
         u64 own[NR][8];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            wb[k] = ro[k] = 0u;
+            wb[k] = ro[k] = sw[k] = 0u;
             qv[k] = 0.f;
             nv[k] = 0;
             ln[k] = 0;
@@ -505,6 +581,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 const int xg = segs[s].x0 + 8 * c;
                 wb[k] = (uint32_t)(segs[s].lbase + 10 * c);
                 ro[k] = (uint32_t)(xg - L.sx0);
+                sw[k] = (uint32_t)(xg >> 4) & 3u;
                 ln[k] = segs[s].line;
                 if constexpr (!kPairs) qv[k] = qs[s];
                 const int rem = a.nx - xg;
@@ -514,6 +591,9 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             for (int r = 0; r < 8; ++r) own[k][r] = nv[k] > 0 ? WS::ld1(wave + wb[k] + phys(r + LT)) : 0ull;
         }
         bool over = false;
+        uint32_t pend[NR];  // outputs the fixup warp wrote in the last step
+#pragma unroll
+        for (int k = 0; k < NR; ++k) pend[k] = 0u;
         for (int t = 0; t < nsteps; ++t) {
             const int z = a.z_begin + t;
             const T* cur = wave + (size_t)(t & 1) * buf;
@@ -521,6 +601,64 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             const float* row = rows + (size_t)(t % kDepthRowSlots) * rowlen;
             const typename TP::E* __restrict__ taps = tap_base(z);
             if (duty && t + kDepthRowSlots - 1 < nsteps) issue_row(t + kDepthRowSlots - 1);
+            if constexpr (kFixW) {
+                float qz[NR];
+                int idx0[NR];
+                uint32_t mk[NR];
+                int cnt = 0;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    qz[k] = qv[k];
+                    if constexpr (kPairs) qz[k] = __int_as_float(ln[k] * a.pair_cnt[z]);
+                    int i1;
+                    idx0[k] = 0;
+                    mk[k] = nv[k] > 0 ? depth_ops<LT, TP, kPairs>(row + ro[k], qz[k], a.nk, nv[k], taps, idx0[k], i1)
+                                      : 0u;
+                    cnt += __popc(mk[k]);
+                }
+                // queue the flagged outputs: one shared-memory atomic per warp
+                if (__any_sync(0xffffffffu, cnt != 0)) {
+                    int incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    int base = 0;
+                    if (lane == 31) base = atomicAdd(qcount, total);
+                    int pos = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+#pragma unroll
+                    for (int k = 0; k < NR; ++k)
+                        if (mk[k]) {
+#pragma unroll
+                            for (int r = 1; r < 8; ++r)
+                                if ((mk[k] >> r) & 1u)
+                                    queue[pos++] = make_uint2(wb[k] | ((uint32_t)r << 28),
+                                                              (uint32_t)depth_op_index<kPairs>(qz[k], row[ro[k] + r], a.nk));
+                        }
+                }
+                __syncwarp();
+                if (lane == 0) depth_mbar_arrive(qbar);
+                // image row z from the step's input values (the outputs the
+                // fixup warp wrote in the last step reloaded first)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    if (pend[k]) {
+#pragma unroll
+                        for (int r = 1; r < 8; ++r)
+                            if ((pend[k] >> r) & 1u) own[k][r] = WS::ld1(cur + wb[k] + phys(r + LT));
+                    }
+                    if (nv[k] > 0)
+                        depth_image_item(img + (size_t)(t & 1) * nchunks * 8 + ((k * a.ncw + warp) * 32 + lane) * 8,
+                                         own[k], nv[k], scale, over, sw[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    if (nv[k] > 0) depth_fir<LT, WS, TP>(cur, nxt, wb[k], idx0[k], nv[k], taps, own[k], mk[k]);
+                    pend[k] = mk[k];
+                }
+            } else {
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 float qz = qv[k];
@@ -528,7 +666,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 // image row z from the step's input values (before own[k] is overwritten)
                 if (nv[k] > 0)
                     depth_image_item(img + (size_t)(t & 1) * nchunks * 8 + ((k * a.ncw + warp) * 32 + lane) * 8,
-                                     own[k], nv[k], scale, over);
+                                     own[k], nv[k], scale, over, sw[k]);
                 int idx1 = -1;
                 uint32_t mask = 0;
                 if (nv[k] > 0)
@@ -544,6 +682,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                         if ((mask >> r) & 1u) own[k][r] = WS::ld1(nxt + wb[k] + phys(r + LT));
                 }
             }
+            }
             fence_proxy_async_smem();  // the image values, for the bulk reduction
             if (duty) {
                 if (t + 1 < nsteps) wait_row(t + 1);
@@ -553,6 +692,34 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             if (duty) issue_image(t);
         }
         if (over) atomicOr(a.status, kStatusOverflow);
+    } else if (fix_warp) {
+        // ---- the fixup warp (queued outputs; row staging and image hand-off)
+        bool ok = true;
+        for (int t = 0; t < nsteps; ++t) {
+            const T* cur = wave + (size_t)(t & 1) * buf;
+            T* nxt = wave + (size_t)((t & 1) ^ 1) * buf;
+            const typename TP::E* __restrict__ taps = tap_base(a.z_begin + t);
+            if (duty) {
+                if (t + kDepthRowSlots - 1 < nsteps) issue_row(t + kDepthRowSlots - 1);
+                if (t + 1 < nsteps) wait_row(t + 1);
+            }
+            if (ok && !mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls)) {
+                ok = false;
+                if (lane == 0) atomicOr(a.status, kStatusTimeout);
+            }
+            const int n = ok ? *reinterpret_cast<volatile int*>(qcount) : 0;
+            for (int i = lane; i < n; i += 32) {
+                const uint2 e = queue[i];
+                const uint32_t wbo = e.x & 0x0fffffffu;
+                const int r = (int)(e.x >> 28);
+                WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)e.y * (LT + 1)));
+            }
+            __syncwarp();
+            if (lane == 0) *qcount = 0;
+            if (duty) depth_bulk_wait_read();
+            step_barrier();
+            if (duty) issue_image(t);
+        }
     } else {
         // ---- the extra warp (halo at the cut, row staging); warps beyond it
         // (a launch sized for wider groups) only keep the step barriers
@@ -593,13 +760,33 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             if (halo && t + 1 < nsteps) {
                 const typename TP::E* __restrict__ taps = tap_base(z);
                 if (t >= 1) {
-                    // send this CTA's time-t values, which the neighbour needs at its step t
-                    if (lane < LT) box[(t & 1) * LT + lane] = cur[c_lbase + phys(x_send + lane + LT)];
-                    // the warp's box writes, then one release-arrive (cumulative
-                    // over what the warp barrier made visible to lane 0)
-                    __syncwarp();
-                    if (lane == 0) depth_mbar_arrive_remote((t & 1) ? nb_inbar1 : nb_inbar0);
-                    // pull the neighbour's time-t values (at step 0 they came from the slab)
+                    // expect the neighbour's time-t values in this CTA's inbox
+                    // [t & 1] (its remote stores count their bytes on
+                    // inbar[t & 1]), and push this CTA's time-t values, which
+                    // the neighbour needs at its step t, into its inbox
+                    if (lane == 0) mbar_arrive_expect_tx(&inbar[t & 1], (uint32_t)(LT * WS::kBytes));
+                    if (lane < LT) {
+                        const T v = cur[c_lbase + phys(x_send + lane + LT)];
+                        const uint32_t dst = nb_box + (uint32_t)(((t & 1) * LT + lane) * WS::kBytes);
+                        const uint32_t bar = (t & 1) ? nb_inbar1 : nb_inbar0;
+                        if constexpr (WS::kBytes == 8) depth_st_async_b64(dst, *reinterpret_cast<const u64*>(&v), bar);
+                        else depth_st_async_b32(dst, *reinterpret_cast<const uint32_t*>(&v), bar);
+                    }
+                }
+                // the redundant output's operator, its taps warmed into L1
+                // while the neighbour's values travel
+                int idx_red = -1;
+                if (lane < LT) {
+                    const int xg = c_x0 + x_red + lane;
+                    if (xg >= 0 && xg < a.nx) {
+                        float qz = c_q;
+                        if constexpr (kPairs) qz = __int_as_float(c_line * a.pair_cnt[z]);
+                        idx_red = depth_op_index<kPairs>(qz, row[xg - L.sx0], a.nk);
+                        depth_prefetch_taps<LT, TP>(taps + (size_t)idx_red * (LT + 1));
+                    }
+                }
+                if (t >= 1) {
+                    // the neighbour's time-t values (at step 0 they came from the slab)
                     const uint32_t par = (uint32_t)(((t - 1) >> 1) & 1);
                     bool ok = mbar_wait_cluster_bounded(&inbar[t & 1], par, halo_ok ? kHaloPolls : 1u);
                     ok = __all_sync(0xffffffffu, ok);
@@ -607,30 +794,13 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                         halo_ok = false;
                         if (lane == 0) atomicOr(a.status, kStatusTimeout);
                     }
-                    if (lane < LT) {
-                        const uint32_t src = nb_box + (uint32_t)(((t & 1) * LT + lane) * WS::kBytes);
-                        T v;
-                        if constexpr (WS::kBytes == 8) {
-                            const u64 u = depth_ld_cluster_b64(src);
-                            v = *reinterpret_cast<const T*>(&u);
-                        } else {
-                            const uint32_t u = depth_ld_cluster_b32(src);
-                            v = *reinterpret_cast<const T*>(&u);
-                        }
-                        const_cast<T*>(cur)[c_lbase + phys(x_pull + lane + LT)] = v;
-                    }
+                    if (lane < LT) const_cast<T*>(cur)[c_lbase + phys(x_pull + lane + LT)] = box[(t & 1) * LT + lane];
                     __syncwarp();
                 }
                 if (lane < LT) {
                     const int x = x_red + lane;
-                    const int xg = c_x0 + x;
                     u64 o = 0ull;
-                    if (xg >= 0 && xg < a.nx) {
-                        float qz = c_q;
-                        if constexpr (kPairs) qz = __int_as_float(c_line * a.pair_cnt[z]);
-                        const int idx = depth_op_index<kPairs>(qz, row[xg - L.sx0], a.nk);
-                        o = fir1<LT, WS, TP>(cur + c_lbase, x, taps + (size_t)idx * (LT + 1));
-                    }
+                    if (idx_red >= 0) o = fir1<LT, WS, TP>(cur + c_lbase, x, taps + (size_t)idx_red * (LT + 1));
                     WS::st1(nxt + c_lbase + phys(x + LT), o);
                 }
             }
@@ -647,7 +817,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     if (duty) depth_bulk_wait_all();
     if (C > 1) cluster_sync_all(); else __syncthreads();
     if (tid == 0) {
-        for (int b = 0; b < kDepthRowSlots + 2; ++b) depth_mbar_inval(&mbar[b]);
+        for (int b = 0; b < kDepthRowSlots + 3; ++b) depth_mbar_inval(&mbar[b]);
     }
     const T* fin = wave + (size_t)(nsteps & 1) * buf;
     for (int s = 0; s < nseg; ++s) {
@@ -661,18 +831,242 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     __syncthreads();
 }
 
-// Threads of a depth-loop launch: ncw compute warps (at most 12 with one item
-// per lane, 8 with two) and the extra warp.
-template <int NR>
+// ---------------------------------------------------------------- decoupled
+// The depth loop with one whole-line group per CTA and no step barrier: every
+// warp runs its own pipeline over its 32 chunks (lane = one 8-output item) and
+// waits only for the two warps whose chunks its windows reach.  Before step
+// t + 1 a warp waits until its neighbours have finished step t: their step-t
+// outputs are its inputs (read after write), and they have finished reading
+// the buffer its step t + 1 overwrites (write after read).  Warps may
+// therefore drift apart by up to one step per warp of distance, so a warp
+// slowed by operator changes delays only its neighbours for a while instead
+// of the whole CTA every step.  The slowness values are staged per lane
+// (cp.async, two steps ahead, ring of kDepthLaneRowSlots); each warp hands its
+// own image chunks to the bulk-copy engine (reduction, add int64) and reuses
+// an imaging buffer slot after that reduction has read it.
+__device__ __forceinline__ void depth_cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void depth_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void depth_cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+__device__ __forceinline__ void depth_bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ int depth_ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void depth_st_release(int* p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(p)), "r"(v) : "memory");
+}
+// Bounded wait (one lane) until prog[a] >= s and prog[b] >= s; false after
+// about kWaitPolls polls (backing off with short sleeps).
+__device__ __forceinline__ bool depth_wait_progress(const int* prog, int a, int b, int s) {
+    for (uint32_t it = 0; it < kWaitPolls; ++it) {
+        if (depth_ld_acquire(prog + a) >= s && depth_ld_acquire(prog + b) >= s) return true;
+        if (it >= 32) __nanosleep(64);
+    }
+    return false;
+}
+
+template <int LT, class WS, class TP, bool kPairs>
+__device__ __forceinline__ void run_depth_warps(const DepthArgs& a, int g, unsigned char* smem) {
+    typedef typename WS::T T;
+    const typename TP::E* __restrict__ taps_all = static_cast<const typename TP::E*>(a.taps);
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nthr >> 5;
+
+    DepthLayout& L = *reinterpret_cast<DepthLayout*>(smem);
+    if (tid == 0) depth_layout(a.nx, a.nxp, a.nw, a.G, 1, g, 0, LT, WS::kBytes, L, true);
+    __syncthreads();
+    const DepthSeg* segs = L.seg;
+    int* prog = reinterpret_cast<int*>(smem + L.off_prog);
+    float* qs = reinterpret_cast<float*>(smem + L.off_qs);
+    float* rows = reinterpret_cast<float*>(smem + L.off_rows);
+    long long* img = reinterpret_cast<long long*>(smem + L.off_img);
+    T* wave = reinterpret_cast<T*>(smem + L.off_wave);
+    const int nseg = L.nseg, buf = L.buf, nchunks = L.nchunks;
+    const int nsteps = a.z_end - a.z_begin;
+    const int wfirst = warp * 32, wend = min(wfirst + 32, nchunks);
+    const bool wactive = wfirst < nchunks;
+
+    // ---- prologue: zero the buffers, line factors, wavefield at z_begin
+    for (int i = tid; i < 2 * buf; i += nthr) wave[i] = WS::zero();
+    if constexpr (!kPairs) {
+        if (tid < nseg) qs[tid] = q_of_line(a.i0, segs[tid].line, a.nt, a.dt, a.dk);
+    }
+    // warps without chunks never hold their neighbours back
+    if (tid < kDepthMaxComputeWarps) prog[tid] = (tid < nwarps && tid * 32 < nchunks) ? -1 : INT_MAX;
+    __syncthreads();
+    for (int s = 0; s < nseg; ++s) {
+        const int line = segs[s].line, x0 = segs[s].x0, lbase = segs[s].lbase;
+        const float2* src = a.slab + (size_t)line * a.nx;
+        const int P = LT + 8 * ((LT + 7) >> 3);
+        const int npos = P + 8 * segs[s].nc + 2 * LT;
+        for (int p = tid; p < npos; p += nthr) {
+            const int x = x0 - P + p;
+            if (x >= 0 && x < a.nx) wave[lbase + phys(x - x0 + LT)] = WS::from_f2(src[x]);
+        }
+    }
+    const float scale = depth_scale(*a.scale_exp);
+    __syncthreads();
+
+    // ---- the lane's item
+    const int item = wfirst + lane;
+    const bool has = item < nchunks;
+    uint32_t wb = 0u, sw = 0u;
+    float qv = 0.f;
+    int nv = 0, ln = 0, xg = 0;
+    if (has) {
+        int s = 0;
+        while (s + 1 < nseg && segs[s + 1].flat <= item) ++s;
+        const int c = item - segs[s].flat;
+        xg = segs[s].x0 + 8 * c;
+        wb = (uint32_t)(segs[s].lbase + 10 * c);
+        sw = (uint32_t)(xg >> 4) & 3u;
+        ln = segs[s].line;
+        if constexpr (!kPairs) qv = qs[s];
+        const int rem = a.nx - xg;
+        nv = rem < 8 ? rem : 8;
+    }
+    u64 own[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) own[r] = nv > 0 ? WS::ld1(wave + wb + phys(r + LT)) : 0ull;
+    const uint32_t ro = (uint32_t)item * 8u;  // the item's values in a row slot
+    // rows of step t: the lane's 8 values, committed as one group per step
+    // (empty groups past the last step keep the count uniform)
+    const float* slow_src = a.slow + (size_t)a.z_begin * a.nxp + xg;
+    auto issue_rows = [&](int t) {
+        if (has && t < nsteps) {
+            float* dst = rows + (size_t)(t % kDepthLaneRowSlots) * nchunks * 8 + ro;
+            const float* src = slow_src + (size_t)t * a.nxp;
+            depth_cp_async16(dst, src);
+            depth_cp_async16(dst + 4, src + 4);
+        }
+        depth_cp_async_commit();
+    };
+    auto tap_base = [&](int z) -> const typename TP::E* {
+        if constexpr (kPairs) return taps_all + (size_t)(a.pair_base[z] - a.pair_base[a.pair_z0]) * (LT + 1);
+        else return taps_all;
+    };
+    const int left = warp > 0 ? warp - 1 : warp, right = warp + 1 < kDepthMaxComputeWarps ? warp + 1 : warp;
+    bool over = false, ok = true;
+    if (wactive) {
+        issue_rows(0);
+        issue_rows(1);
+        for (int t = 0; t < nsteps; ++t) {
+            const int z = a.z_begin + t;
+            const T* cur = wave + (size_t)(t & 1) * buf;
+            T* nxt = wave + (size_t)((t & 1) ^ 1) * buf;
+            const float* row = rows + (size_t)(t % kDepthLaneRowSlots) * nchunks * 8;
+            long long* imgt = img + (size_t)(t & 1) * nchunks * 8;
+            issue_rows(t + 2);
+            depth_cp_async_wait<2>();                 // this lane's row values of step t
+            if (lane == 0 && t >= 2) depth_bulk_wait_read1();  // the reduction of step t - 2 has read imgt
+            __syncwarp();
+            // image row z from the step's input values, handed to the bulk-copy engine
+            if (has) depth_image_item(imgt + (size_t)item * 8, own, nv, scale, over, sw);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                unsigned long long* dst = a.acc + (size_t)z * a.nxp;
+                for (int s = 0; s < nseg; ++s) {
+                    const int lo = max(wfirst, segs[s].flat), hi = min(wend, segs[s].flat + segs[s].nc);
+                    if (lo < hi)
+                        depth_bulk_reduce_add_u64(dst + segs[s].x0 + 8 * (lo - segs[s].flat), imgt + (size_t)lo * 8,
+                                                  (uint32_t)(hi - lo) * 64u);
+                }
+                depth_bulk_commit();
+                // the neighbours have finished step t - 1
+                if (t >= 1 && ok && !depth_wait_progress(prog, left, right, t - 1)) {
+                    ok = false;
+                    atomicOr(a.status, kStatusTimeout);
+                }
+            }
+            __syncwarp();
+            float qz = qv;
+            if constexpr (kPairs) qz = __int_as_float(ln * a.pair_cnt[z]);
+            const typename TP::E* __restrict__ taps = tap_base(z);
+            int idx1 = -1;
+            uint32_t mask = 0;
+            if (nv > 0) mask = depth_item<LT, WS, TP, kPairs>(cur, nxt, wb, row + ro, qz, a.nk, nv, taps, own, idx1);
+            if (__any_sync(0xffffffffu, mask != 0u)) {
+                __syncwarp();
+                depth_fixups<LT, WS, TP, kPairs>(mask, wb, ro, qz, idx1, cur, nxt, row, a.nk, taps, lane);
+                __syncwarp();
+#pragma unroll
+                for (int r = 1; r < 8; ++r)
+                    if ((mask >> r) & 1u) own[r] = WS::ld1(nxt + wb + phys(r + LT));
+            }
+            __syncwarp();  // the warp's outputs of step t are all written
+            if (lane == 0) depth_st_release(prog + warp, t);
+        }
+        if (lane == 0) depth_bulk_wait_all();
+    }
+    depth_cp_async_wait<0>();
+    if (over) atomicOr(a.status, kStatusOverflow);
+    __syncthreads();
+    const T* fin = wave + (size_t)(nsteps & 1) * buf;
+    for (int s = 0; s < nseg; ++s) {
+        const int x0 = segs[s].x0, lbase = segs[s].lbase;
+        float2* dst = a.slab + (size_t)segs[s].line * a.nx + x0;
+        const int n = (a.nx - x0) < 8 * segs[s].nc ? (a.nx - x0) : 8 * segs[s].nc;
+        for (int x = tid; x < n; x += nthr) dst[x] = WS::to_f2(fin[lbase + phys(x + LT)]);
+    }
+    __syncthreads();
+}
+
+// Threads of a depth-loop launch compiled for OCC resident CTAs per SM.
+// OCC = 1: ncw compute warps (at most 12 with one item per lane, 8 with two),
+// the extra (halo) warp and the fixup warp.  OCC = 2 (whole lines, no cut, no extra warp): at most 8
+// compute warps with one item per lane, so that two CTAs (16 warps, 4 per SM
+// sub-partition at 128 registers a thread) share an SM and each one's step
+// barrier, imaging and fixups overlap the other's FIR.
+template <int NR, int OCC = 1>
 struct DepthWarps {
-    static constexpr int kMaxCompute = NR == 1 ? kDepthMaxComputeWarps : 8;
-    static constexpr int kThreads = (kMaxCompute + 1) * 32;
+    static_assert(OCC == 1 || (OCC == 2 && NR == 1), "two CTAs per SM: one item per lane");
+    static constexpr int kMaxCompute = (NR == 1 && OCC == 1) ? kDepthMaxComputeWarps : 8;
+    static constexpr int kThreads = OCC == 1 ? (kMaxCompute + 2) * 32 : kMaxCompute * 32;
 };
 
-template <int LT, class WS, class TP, int NR, bool kPairs = false>
-__global__ void __launch_bounds__(DepthWarps<NR>::kThreads, 1) k_depth(const DepthArgs a) {
+template <int LT, class WS, class TP, int NR, bool kPairs = false, int OCC = 1>
+__global__ void __launch_bounds__(DepthWarps<NR, OCC>::kThreads, OCC) k_depth(const DepthArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_depth<LT, WS, TP, NR, kPairs>(a, (int)(blockIdx.x / a.C), smem);
+    if constexpr (OCC == 2) run_depth_warps<LT, WS, TP, kPairs>(a, (int)blockIdx.x, smem);
+    else run_depth<LT, WS, TP, NR, kPairs>(a, (int)(blockIdx.x / a.C), smem);
+}
+
+// Launch of the depth loop for a plan (plan_depth): the kernel compiled for
+// the plan's items per lane and CTAs per SM, clusters of plan.cluster CTAs.
+template <int LT, class WS, class TP, int NR, bool kPairs, int OCC>
+inline cudaError_t launch_depth_nr(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
+    auto kern = k_depth<LT, WS, TP, NR, kPairs, OCC>;
+    cudaError_t e = ensure_smem(kern, plan.smem, false);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.groups * plan.cluster);
+    cfg.blockDim = dim3((plan.warps + plan.extra + plan.fixw) * 32);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = plan.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = plan.cluster > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int LT, class WS, class TP, bool kPairs>
+inline cudaError_t launch_depth(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
+    if (plan.occ == 2) {
+        if (plan.nr != 1 || plan.extra || plan.cluster != 1) return cudaErrorInvalidValue;
+        return launch_depth_nr<LT, WS, TP, 1, kPairs, 2>(plan, a, s);
+    }
+    if (plan.nr == 1) return launch_depth_nr<LT, WS, TP, 1, kPairs, 1>(plan, a, s);
+    if (plan.nr == 2) return launch_depth_nr<LT, WS, TP, 2, kPairs, 1>(plan, a, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fxmig_impl

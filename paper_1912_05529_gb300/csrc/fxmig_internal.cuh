@@ -35,7 +35,17 @@ constexpr int kWsNormCount = 2;  // int index of the finished line-norm blocks
 // e[nz] int32.  Every frequency's contribution is converted on its own
 // (image_fixed) and the integer sums do not depend on the order of the
 // additions, so the image is deterministic whatever the launch shape.
+// Within a row the four value pairs of 8-value chunk c are stored in the order
+// p ^ ((c >> 1) & 3) (acc_slot): when the lanes of a warp store pair p of 32
+// consecutive chunks (16 bytes each) into a shared-memory copy of the row,
+// every 8 lanes cover all 32 banks (4 wavefronts, the minimum, instead of 16),
+// and every chunk still occupies its own 64 bytes, so a run of chunks is one
+// contiguous bulk reduction.
 inline int slow_pitch(int nx) { return (nx + 7) & ~7; }
+__host__ __device__ __forceinline__ int acc_slot(int x) {
+    const int c = x >> 3;
+    return (c << 3) | ((((x >> 1) & 3) ^ ((c >> 1) & 3)) << 1) | (x & 1);
+}
 inline int image_planes(int nx) {
     const long long bytes = 8LL * slow_pitch(nx) + 4;  // per depth row
     return (int)((bytes + 4LL * nx - 1) / (4LL * nx));
@@ -224,6 +234,8 @@ struct MigratePlan {
     int lines;     // persistent: max lines per group
     size_t smem;   // dynamic shared memory bytes per CTA
     int nparts;    // planes of the image accumulator (image_planes(nx))
+    int occ;       // persistent: CTAs resident per SM the kernel is compiled for (1, or 2 for whole lines)
+    int fixw;      // persistent: a fixup warp per CTA recomputes the outputs whose operator changes
 };
 
 // slow_pitch(nx) is also the row pitch of the slowness field in the
@@ -241,8 +253,9 @@ size_t t2f_ws_bytes(const fxmig_desc* d);
 bool t2f_supported(int nt);
 
 // Plan of the persistent depth loop (depth.cuh) for storage of esize bytes
-// per value; req_*: requested cluster size, groups, compute warps (0 = auto).
-int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int req_w, MigratePlan* p);
+// per value; req_*: requested cluster size, groups, compute warps, CTAs per
+// SM (0 = auto).
+int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int req_w, int req_o, MigratePlan* p);
 // Per call, before a depth loop: the image scale exponent from the wavefield
 // (written to ws[kWsScaleExp] and to the scale rows [z_begin, z_end) of the
 // accumulator) and zeroed accumulator rows.  norms: nw doubles of scratch;

@@ -26,13 +26,14 @@
 
 namespace fxmig_impl {
 
-// image[z][x] = acc[z][x] * 2^-e[z]  (HBM-bound: 12 bytes per pixel)
+// image[z][x] = acc[z][acc_slot(x)] * 2^-e[z]  (HBM-bound: 12 bytes per pixel;
+// a warp reads 32 consecutive pixels from 4 whole chunks)
 __global__ void __launch_bounds__(256) k_image_fixed(const long long* __restrict__ acc, const int* __restrict__ e,
                                                       int nz, int nx, int pitch, float* __restrict__ image) {
     const size_t n = (size_t)nz * nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int z = (int)(i / (size_t)nx), x = (int)(i - (size_t)z * nx);
-        image[i] = (float)ldexp((double)__ldcs(acc + (size_t)z * pitch + x), -__ldg(e + z));
+        image[i] = (float)ldexp((double)__ldcs(acc + (size_t)z * pitch + acc_slot(x)), -__ldg(e + z));
     }
 }
 

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_migrate_step(const StepArgs
         if (x < a.nx) {
             long long s = 0;
             for (int w = 0; w < kStepWarps; ++w) s += imgw[w * kStepTile + tid];
-            if (s) depth_red_add_u64(a.acc + (size_t)z * a.nxp + x, s);
+            if (s) depth_red_add_u64(a.acc + (size_t)z * a.nxp + acc_slot(x), s);
         }
     }
 }
@@ -192,6 +192,16 @@ int device_smem_optin() {
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v > 0 ? v : 227 * 1024;
 }
+// dynamic shared memory each of two CTAs resident on one SM may use
+int device_smem_half() {
+    int dev = 0, sm = 0, res = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (sm <= 0) sm = 228 * 1024;
+    if (res < 0) res = 1024;
+    return sm / 2 - res;
+}
 }  // namespace
 
 size_t migrate_ws_bytes(const fxmig_desc* d) {
@@ -206,15 +216,23 @@ size_t migrate_ws_bytes_persistent(const fxmig_desc* d) {
     return migrate_ws_layout(d, LT).slab2;
 }
 
-int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int req_w, MigratePlan* p) {
+int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int req_w, int req_o,
+               MigratePlan* p) {
     const int sms = device_sms();
     const size_t smax = (size_t)device_smem_optin();
+    const size_t shalf = (size_t)std::max(0, device_smem_half());
     const int nxp = slow_pitch(d->nx);
     double best = 1e300;
     bool found = false;
-    for (int C : {2, 1}) {
+    // (cluster, CTAs per SM): cut lines in clusters of 2, whole lines one or
+    // two CTAs per SM
+    const int cand[3][2] = {{2, 1}, {1, 1}, {1, 2}};
+    for (const auto& cc : cand) {
+        const int C = cc[0], occ = cc[1];
         if (req_c && C != req_c) continue;
-        const int per_wave = std::max(1, C == 1 ? sms : sms / 2);
+        if (req_o && occ != req_o) continue;
+        const int per_wave = std::max(1, occ * (C == 1 ? sms : sms / 2));
+        const int wmax = occ == 2 ? DepthWarps<1, 2>::kMaxCompute : DepthWarps<1>::kMaxCompute;
         const int m_max = std::min(d->nw, 2 * kDepthMaxSegs - 2);
         for (int m = 1; m <= m_max; ++m) {
             const int G = req_g ? std::min(req_g, d->nw) : (d->nw + m - 1) / m;
@@ -225,31 +243,47 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
             DepthLayout L;
             for (int g = 0; g < G && ok; ++g)
                 for (int r = 0; r < C && ok; ++r) {
-                    ok = depth_layout(d->nx, nxp, d->nw, G, C, g, r, LT, esize, L);
+                    ok = depth_layout(d->nx, nxp, d->nw, G, C, g, r, LT, esize, L, occ == 2);
                     if (!ok) break;
                     maxch = std::max(maxch, L.nchunks);
                     cut |= L.cutseg >= 0 ? 1 : 0;
                     smem = std::max(smem, L.total);
                 }
-            if (!ok || smem > smax || maxch == 0) {
+            if (!ok || smem > (occ == 2 ? shalf : smax) || maxch == 0) {
                 if (req_g) break;
                 continue;
             }
             int nr = 0, ncw = 0;
-            if (maxch <= 32 * DepthWarps<1>::kMaxCompute) {
+            if (maxch <= 32 * wmax) {
                 nr = 1;
                 ncw = (maxch + 31) / 32;
-            } else if (maxch <= 64 * DepthWarps<2>::kMaxCompute) {
+            } else if (occ == 1 && maxch <= 64 * DepthWarps<2>::kMaxCompute) {
                 nr = 2;
                 ncw = (maxch + 63) / 64;
             }
             if (req_w) {
-                if (req_w * 32 >= maxch && req_w <= DepthWarps<1>::kMaxCompute) {
+                if (req_w * 32 >= maxch && req_w <= wmax) {
                     nr = 1;
                     ncw = req_w;
-                } else if (req_w * 64 >= maxch && req_w <= DepthWarps<2>::kMaxCompute) {
+                } else if (occ == 1 && req_w * 64 >= maxch && req_w <= DepthWarps<2>::kMaxCompute) {
                     nr = 2;
                     ncw = req_w;
+                } else {
+                    nr = 0;
+                }
+            }
+            // one item per lane (one CTA per SM): a fixup warp and its queue
+            int fixw = 0;
+            if (nr == 1 && occ == 1) {
+                size_t sf = 0;
+                for (int g = 0; g < G; ++g)
+                    for (int r = 0; r < C; ++r) {
+                        depth_layout(d->nx, nxp, d->nw, G, C, g, r, LT, esize, L, false, true);
+                        sf = std::max(sf, L.total);
+                    }
+                if (sf <= smax) {
+                    fixw = 1;
+                    smem = sf;
                 } else {
                     nr = 0;
                 }
@@ -259,9 +293,15 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
                 continue;
             }
             // per depth step: warp items on the busiest SM sub-partition, plus
-            // the step's fixed costs; waves of groups run one after another
+            // the step's fixed costs (barrier, imaging, operator changes; with
+            // a cut, the extra warp's exchange); waves of groups run one after
+            // another.  Calibrated on 2048-trace lines (221 frequencies): the
+            // cut plan (1.5 lines per SM) 2.55 ms, two whole-line CTAs per SM
+            // 3.07 ms.
             const int waves = (G + per_wave - 1) / per_wave;
-            const double cost = (double)waves * (nr * ((ncw + 3) / 4) + 0.35);
+            const int resident = std::min(occ, (G + (C == 1 ? sms : sms / 2) - 1) / (C == 1 ? sms : sms / 2));
+            const double fixed = (occ == 2 ? 1.0 : 0.35) + ((C > 1 && cut) ? 0.5 : 0.0);
+            const double cost = (double)waves * (nr * ((resident * ncw + 3) / 4) + fixed);
             if (cost < best - 1e-9) {
                 best = cost;
                 found = true;
@@ -273,6 +313,8 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
                 p->lines = (d->nw + G - 1) / G;
                 p->smem = smem;
                 p->nparts = image_planes(d->nx);
+                p->occ = occ;
+                p->fixw = fixw;
             }
             if (req_g) break;
         }
@@ -311,34 +353,9 @@ int plan_migrate(const fxmig_desc* d, const fxmig_launch* launch, MigratePlan* p
     const int req_w = launch ? launch->warps : 0;
     if (req_w < 0 || req_w > kDepthMaxComputeWarps) return FXMIG_EINVAL;
     const int req_g = (launch && launch->groups > 0) ? launch->groups : 0;
-    return plan_depth(d, LT, prec == FXMIG_PREC_FP32 ? 8 : 4, req_c, req_g, req_w, p);
-}
-
-template <int LT, class WS, class TP, int NR, bool kPairs>
-cudaError_t launch_depth_nr(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
-    auto kern = k_depth<LT, WS, TP, NR, kPairs>;
-    cudaError_t e = ensure_smem(kern, plan.smem, false);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.groups * plan.cluster);
-    cfg.blockDim = dim3((plan.warps + plan.extra) * 32);
-    cfg.dynamicSmemBytes = plan.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = plan.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <int LT, class WS, class TP, bool kPairs>
-cudaError_t launch_depth(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
-    if (plan.nr == 1) return launch_depth_nr<LT, WS, TP, 1, kPairs>(plan, a, s);
-    if (plan.nr == 2) return launch_depth_nr<LT, WS, TP, 2, kPairs>(plan, a, s);
-    return cudaErrorInvalidValue;
+    const int req_o = launch ? launch->ctas_per_sm : 0;
+    if (req_o < 0 || req_o > 2 || (req_o == 2 && req_c == 2)) return FXMIG_EINVAL;
+    return plan_depth(d, LT, prec == FXMIG_PREC_FP32 ? 8 : 4, req_c, req_g, req_w, req_o, p);
 }
 
 DepthArgs depth_args(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* slow, const void* taps,
@@ -354,7 +371,7 @@ DepthArgs depth_args(const fxmig_desc* d, const MigratePlan& plan, void* slab, c
     a.acc = reinterpret_cast<unsigned long long*>(partials);
     a.scale_exp = head + kWsScaleExp;
     a.status = head;
-    a.C = plan.cluster; a.G = plan.groups; a.ncw = plan.warps; a.extra = plan.extra;
+    a.C = plan.cluster; a.G = plan.groups; a.ncw = plan.warps; a.extra = plan.extra; a.fixw = plan.fixw;
     return a;
 }
 

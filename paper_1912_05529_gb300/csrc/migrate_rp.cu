@@ -46,25 +46,7 @@ cudaError_t expand_taps_rp(int precision, const float2* table, int nk, int L, in
 
 template <int LT, class WS, class TP>
 static cudaError_t launch_one(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
-    auto kern1 = k_depth<LT, WS, TP, 1, false>;
-    auto kern2 = k_depth<LT, WS, TP, 2, false>;
-    auto kern = plan.nr == 1 ? kern1 : kern2;
-    if (plan.nr != 1 && plan.nr != 2) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_smem(kern, plan.smem, false);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.groups * plan.cluster);
-    cfg.blockDim = dim3((plan.warps + plan.extra) * 32);
-    cfg.dynamicSmemBytes = plan.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = plan.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
+    return launch_depth<LT, WS, TP, false>(plan, a, s);
 }
 
 template <int LT>

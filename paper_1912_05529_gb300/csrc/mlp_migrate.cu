@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_step_pairs(const PairStepAr
         if (x < a.nx) {
             long long s = 0;
             for (int w = 0; w < kPairWarps; ++w) s += imgw[w * kPairTile + tid];
-            if (s) depth_red_add_u64(a.acc + (size_t)z * a.pitch + x, s);
+            if (s) depth_red_add_u64(a.acc + (size_t)z * a.pitch + acc_slot(x), s);
         }
     }
 }
@@ -229,7 +229,7 @@ int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p) {
     p->LT = LT;
     // persistent form (pair-index rows staged like slowness rows) when the
     // lines can be planned; one launch per row otherwise
-    p->persistent = plan_depth(d, LT, 8, 0, 0, 0, &p->pplan) == FXMIG_OK ? 1 : 0;
+    p->persistent = plan_depth(d, LT, 8, 0, 0, 0, 0, &p->pplan) == FXMIG_OK ? 1 : 0;
     p->groups = p->persistent ? p->pplan.groups : std::max(1, std::min(d->nw, 16));
     p->nparts = image_planes(d->nx);
     // rows per operator block: worst-case operator storage (every point of a
@@ -305,24 +305,7 @@ static cudaError_t launch_pair_steps(const fxmig_desc* d, const MlpMigratePlan& 
 
 template <int LT>
 static cudaError_t launch_pairs(const MigratePlan& pp, const DepthArgs& pa, cudaStream_t s) {
-    auto kern1 = k_depth<LT, WsF32, TapF32, 1, true>;
-    auto kern2 = k_depth<LT, WsF32, TapF32, 2, true>;
-    auto kern = pp.nr == 1 ? kern1 : kern2;
-    cudaError_t e = ensure_smem(kern, pp.smem, false);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pp.groups * pp.cluster);
-    cfg.blockDim = dim3((pp.warps + pp.extra) * 32);
-    cfg.dynamicSmemBytes = pp.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = pp.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, pa);
+    return launch_depth<LT, WsF32, TapF32, true>(pp, pa, s);
 }
 
 cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, void* slab, const float* vel,
@@ -372,6 +355,7 @@ cudaError_t launch_mlp_migrate(const fxmig_desc* d, const MlpMigratePlan& plan, 
         pa.scale_exp = w.head + kWsScaleExp;
         pa.status = w.head;
         pa.C = plan.pplan.cluster; pa.G = plan.pplan.groups; pa.ncw = plan.pplan.warps; pa.extra = plan.pplan.extra;
+        pa.fixw = plan.pplan.fixw;
         pa.pair_cnt = w.cnt;
         pa.pair_base = w.base;
     }

@@ -153,14 +153,19 @@ def test_large_problem_plans_several_waves(fx):
 
 
 def test_bench_workload_shape(fx):
-    # 2048 traces x 221 frequencies: 76 clusters of 2 over 152 SMs, groups of
+    # 2048 traces x 221 frequencies: 74 clusters of 2 over 152 SMs, groups of
     # 2 or 3 lines laid end to end and cut in half (one cut line per CTA), one
-    # item per compute lane
+    # item per compute lane; on request, one whole line per CTA and two CTAs
+    # per SM
     d = fx.desc_for(nx=2048, nz=800, nt=2000, dx=12.5, dz=5.0, dt=0.002, f_lo=5.0, f_hi=60.0, L=12,
                     v_min=750.0)
     s = fx.fxmig_launch_shape(d)
-    assert (s.cluster, s.items_per_lane, s.warps) == (2, 1, 12)
-    assert 2 * s.groups >= 140 and s.waves == 1
+    assert (s.cluster, s.ctas_per_sm, s.items_per_lane, s.warps) == (2, 1, 1, 12)
+    assert 2 * s.groups >= 140 and s.waves == 1 and s.smem_bytes <= 227 * 1024
+    o = fx.fxmig_launch_shape(d, fx.Launch(ctas_per_sm=2))
+    assert (o.cluster, o.ctas_per_sm, o.items_per_lane, o.warps) == (1, 2, 1, 8)
+    assert o.groups == 221 and o.waves == 1
+    assert 2 * o.smem_bytes <= 228 * 1024 - 2048
     pd = fx.fxmig_launch_shape(d, fx.Launch(mode=fx.FXMIG_MODE_PER_DEPTH))
     assert pd.mode == fx.FXMIG_MODE_PER_DEPTH and pd.ctas == 8 * pd.groups
 

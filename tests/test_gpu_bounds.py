@@ -67,7 +67,8 @@ def _guarded_migrate(fx, w, pr, launch):
     return slab.t.cpu().numpy(), image.t.cpu().numpy()
 
 
-LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=2, groups=19),
+LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, ctas_per_sm=2), dict(mode=1, cluster=2),
+            dict(mode=1, cluster=2, groups=19),
             dict(mode=1, cluster=2, groups=56, warps=1), dict(mode=1, precision=1),
             dict(mode=1, cluster=2, groups=19, precision=4), dict(mode=2)]
 

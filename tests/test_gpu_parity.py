@@ -88,7 +88,8 @@ def test_t2f_matches_oracle_dft(fx, nx, nt, i0, nw):
 # line cut in half, two waves of CTAs); per-depth launches.
 LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1, cluster=2, groups=37),
             dict(mode=1, cluster=2, groups=15, warps=6), dict(mode=1, cluster=2, groups=112),
-            dict(mode=1, cluster=1, groups=200), dict(mode=2), dict(mode=2, groups=3)]
+            dict(mode=1, cluster=1, groups=200), dict(mode=1, ctas_per_sm=2), dict(mode=1, ctas_per_sm=2, groups=56),
+            dict(mode=2), dict(mode=2, groups=3)]
 
 
 @pytest.fixture(scope="module")
