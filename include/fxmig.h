@@ -233,16 +233,21 @@ int fxmig_image(const fxmig_desc *d, const float *partials, int nparts, float *i
  * handed buffers but no allocator, a real-time path that must not call
  * cudaMalloc because it may synchronise the device).  It computes exactly what
  * fxmig_migrate_ex computes with mode FXMIG_MODE_PERSISTENT and automatic
- * choices (same arguments, same partial-image layout and count), but keeps its
- * scratch (status word and expanded operator table) in a fixed 1 MiB
- * device array inside the library, held on every GPU that loads the library
- * until the process exits.  It allocates and frees nothing.
- *   Limit: nk * (LT + 1) * 16 + 256 <= 1 MiB, where LT is the compiled half
- *   length (4, 8, 12, 16, 17 or 20) at or above L; e.g. nk = 1024 fits every
- *   L <= 20.  Larger problems return FXMIG_ENOSPC without enqueuing anything.
+ * choices (same arguments, same image accumulator layout and count), but keeps
+ * its scratch (status word, expanded operator table, slowness field and the
+ * frequency-line norms of the image scale) in a fixed 8 MiB device array
+ * inside the library, held on every GPU that loads the library until the
+ * process exits.  It allocates and frees nothing.
+ *   Limit: 256 + nk (LT + 1) 16 + nz round8(nx) 4 + nw 8 bytes (each part
+ *   rounded up to 256) <= 8 MiB, where LT is the compiled half length (4, 8,
+ *   12, 16, 17 or 20) at or above L; e.g. nk = 1024, L = 12, 2048 traces and
+ *   800 depths need 6.8 MiB.  Larger problems return FXMIG_ENOSPC without
+ *   enqueuing anything.
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept for the life of the
+ *   process: after cudaDeviceReset on a device, do not call this entry point
+ *   on that device again.
  *   Sharing: all calls on a device share the one array and the last call's
  *   contents stay in it; each call rewrites what it reads, but calls that can
  *   overlap on the GPU (different streams, concurrent graphs) race with each

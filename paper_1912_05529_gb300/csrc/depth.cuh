@@ -145,7 +145,7 @@ __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int
     L.off_mbar = o;
     o += 8 * (kDepthRowSlots + 3);                         // row ring, inbox [parity], fixup queue
     L.off_prog = o;
-    o += 4 * kDepthMaxComputeWarps;                        // decoupled form: last step done per warp
+    o += 4 * kDepthMaxComputeWarps;  // decoupled form: last step done per warp; cut: halo stop flag
     L.off_qs = o;
     o += 4 * kDepthMaxSegs;
     L.off_box = align16(o);
@@ -419,6 +419,9 @@ __device__ __forceinline__ void depth_st_async_b32(uint32_t addr, uint32_t v, ui
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
                  :: "r"(addr), "r"(v), "r"(remote_bar) : "memory");
 }
+__device__ __forceinline__ void depth_st_cluster_b32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.b32 [%0], %1;" :: "r"(addr), "r"(v) : "memory");
+}
 __device__ __forceinline__ u64 depth_ld_cluster_b64(uint32_t addr) {
     u64 v;
     asm volatile("ld.shared::cluster.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
@@ -479,6 +482,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.off_mbar);
     uint64_t* inbar = mbar + kDepthRowSlots;  // [parity]
     uint64_t* qbar = mbar + kDepthRowSlots + 2;
+    int* hstop = reinterpret_cast<int*>(smem + L.off_prog);  // cut: the neighbour gave up the exchange
     int* qcount = reinterpret_cast<int*>(smem + L.off_queue);
     uint2* queue = reinterpret_cast<uint2*>(smem + L.off_queue + 16);
     float* qs = reinterpret_cast<float*>(smem + L.off_qs);
@@ -498,6 +502,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
         for (int b = 0; b < kDepthRowSlots; ++b) mbar_init(&mbar[b], 1);
         for (int b = 0; b < 2; ++b) mbar_init(&inbar[b], 1);  // the local expect_tx arrival (plus the bytes)
         mbar_init(qbar, (uint32_t)a.ncw);                      // every compute warp, once per step
+        *hstop = 0;
         if (kFixW) *qcount = 0;
         fence_mbar_init();
     }
@@ -728,7 +733,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
         int c_lbase = 0, c_x0 = 0, c_line = 0;
         float c_q = 0.f;
         int x_send = 0, x_pull = 0, x_red = 0;
-        uint32_t nb_box = 0u, nb_inbar0 = 0u, nb_inbar1 = 0u;
+        uint32_t nb_box = 0u, nb_inbar0 = 0u, nb_inbar1 = 0u, nb_hstop = 0u;
         if (halo) {
             const bool left = (segs[cs].cut & kCutLeft) != 0;
             const int nc = segs[cs].nc;
@@ -747,6 +752,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             nb_box = map_cluster_rank(box, nb);
             nb_inbar0 = map_cluster_rank(&inbar[0], nb);
             nb_inbar1 = map_cluster_rank(&inbar[1], nb);
+            nb_hstop = map_cluster_rank(hstop, nb);
         }
         bool halo_ok = true;
         for (int t = 0; t < nsteps; ++t) {
@@ -759,13 +765,14 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             // never read)
             if (halo && t + 1 < nsteps) {
                 const typename TP::E* __restrict__ taps = tap_base(z);
-                if (t >= 1) {
+                if (t >= 1 && halo_ok) {
                     // expect the neighbour's time-t values in this CTA's inbox
                     // [t & 1] (its remote stores count their bytes on
                     // inbar[t & 1]), and push this CTA's time-t values, which
                     // the neighbour needs at its step t, into its inbox
+                    // (unless the neighbour has given up waiting)
                     if (lane == 0) mbar_arrive_expect_tx(&inbar[t & 1], (uint32_t)(LT * WS::kBytes));
-                    if (lane < LT) {
+                    if (lane < LT && *reinterpret_cast<volatile int*>(hstop) == 0) {
                         const T v = cur[c_lbase + phys(x_send + lane + LT)];
                         const uint32_t dst = nb_box + (uint32_t)(((t & 1) * LT + lane) * WS::kBytes);
                         const uint32_t bar = (t & 1) ? nb_inbar1 : nb_inbar0;
@@ -785,14 +792,20 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                         depth_prefetch_taps<LT, TP>(taps + (size_t)idx_red * (LT + 1));
                     }
                 }
-                if (t >= 1) {
+                if (t >= 1 && halo_ok) {
                     // the neighbour's time-t values (at step 0 they came from the slab)
                     const uint32_t par = (uint32_t)(((t - 1) >> 1) & 1);
-                    bool ok = mbar_wait_cluster_bounded(&inbar[t & 1], par, halo_ok ? kHaloPolls : 1u);
+                    bool ok = mbar_wait_cluster_bounded(&inbar[t & 1], par, kHaloPolls);
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) {
+                        // give up the exchange for the rest of the launch: tell
+                        // the neighbour to stop pushing (the results are then
+                        // wrong, and the status says so)
                         halo_ok = false;
-                        if (lane == 0) atomicOr(a.status, kStatusTimeout);
+                        if (lane == 0) {
+                            atomicOr(a.status, kStatusTimeout);
+                            depth_st_cluster_b32(nb_hstop, 1u);
+                        }
                     }
                     if (lane < LT) const_cast<T*>(cur)[c_lbase + phys(x_pull + lane + LT)] = box[(t & 1) * LT + lane];
                     __syncwarp();
@@ -811,6 +824,11 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             step_barrier();
             if (duty) issue_image(t);
         }
+        // after an abandoned exchange, give pushes the neighbour issued
+        // before it saw the stop flag time to land (bounded) before this
+        // CTA's shared memory is released
+        if (halo && (!halo_ok || *reinterpret_cast<volatile int*>(hstop) != 0))
+            for (int i = 0; i < 256; ++i) __nanosleep(1000);
     }
     // the last image row has reached global memory; no remote access is
     // outstanding once every CTA of the cluster is here

@@ -19,7 +19,10 @@
 #include <float.h>
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "depth.cuh"
 #include "fir.cuh"
@@ -83,7 +86,17 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_migrate_step(const StepArgs
         __syncwarp();
         float re[8];
         u64 res[8];
-        fir8<LT>(wb + lane * 10, s8, q_of_line(a.i0, l, a.nt, a.dt, a.dk), a.nk, a.taps, res, re);
+        // one tap load per tap for 8 outputs where the whole warp's outputs
+        // share their operator; per-output operators otherwise
+        const float q = q_of_line(a.i0, l, a.nt, a.dt, a.dk);
+        const int idx0 = table_index(q, s8[0], a.nk);
+        bool uni = true;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) uni &= table_index(q, s8[r], a.nk) == idx0;
+        if (__all_sync(0xffffffffu, uni))
+            fir8_shared_taps<LT, WsF32, TapF32>(wb + lane * 10, a.taps + (size_t)idx0 * (LT + 1), res, re);
+        else
+            fir8<LT>(wb + lane * 10, s8, q, a.nk, a.taps, res, re);
 #pragma unroll
         for (int r = 0; r < 8; ++r) acc[r] += image_fixed(re[r], scale, over);
         float2* dst = a.out + (size_t)l * a.nx;
@@ -375,13 +388,103 @@ DepthArgs depth_args(const fxmig_desc* d, const MigratePlan& plan, void* slab, c
     return a;
 }
 
+// The per-depth form's launches as one CUDA graph: captured on a private
+// stream the first time a given set of arguments is seen, instantiated, and
+// replayed on the caller's stream (the graph's kernel arguments hold every
+// pointer, so an identical call can replay it).  A few graphs are kept per
+// process (least recently used dropped).  A caller stream that is itself being
+// captured gets the launches directly.
+namespace {
+struct StepGraphKey {
+    int dev, LT, nx, nz, nw, nk, i0, nt, G, z_begin, z_end;
+    double dt, dk;
+    const void *slab, *slow, *taps, *partials, *head, *ws_slab;
+    bool operator==(const StepGraphKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+struct StepGraph {
+    StepGraphKey key;
+    cudaGraphExec_t exec;
+    unsigned long long used;
+};
+std::mutex g_step_graph_mu;
+StepGraph g_step_graphs[8];
+int g_step_graph_n = 0;
+unsigned long long g_step_graph_tick = 0;
+cudaStream_t g_capture_stream[64] = {};
+}  // namespace
+
+template <int LT>
+static cudaError_t enqueue_per_depth(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* slow,
+                                     const float4* taps, float* partials, int z_begin, int z_end, int* head,
+                                     float2* ws_slab, cudaStream_t s);
+
 template <int LT>
 static cudaError_t launch_per_depth(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* slow,
                                     const float4* taps, float* partials, int z_begin, int z_end, int* head,
                                     float2* ws_slab, cudaStream_t s) {
-    auto kern = k_migrate_step<LT>;
-    cudaError_t e = ensure_smem(kern, plan.smem);
+    cudaError_t e = ensure_smem(k_migrate_step<LT>, plan.smem);
     if (e != cudaSuccess) return e;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone)
+        return enqueue_per_depth<LT>(d, plan, slab, slow, taps, partials, z_begin, z_end, head, ws_slab, s);
+    StepGraphKey key;
+    memset(&key, 0, sizeof(key));
+    e = cudaGetDevice(&key.dev);
+    if (e != cudaSuccess) return e;
+    if (key.dev < 0 || key.dev >= 64)
+        return enqueue_per_depth<LT>(d, plan, slab, slow, taps, partials, z_begin, z_end, head, ws_slab, s);
+    key.LT = LT; key.nx = d->nx; key.nz = d->nz; key.nw = d->nw; key.nk = d->nk; key.i0 = d->i0; key.nt = d->nt;
+    key.G = plan.groups; key.z_begin = z_begin; key.z_end = z_end;
+    key.dt = d->dt; key.dk = d->nk > 1 ? d->k_max / (double)(d->nk - 1) : 0.0;
+    key.slab = slab; key.slow = slow; key.taps = taps; key.partials = partials; key.head = head;
+    key.ws_slab = ws_slab;
+    std::lock_guard<std::mutex> lock(g_step_graph_mu);
+    for (int i = 0; i < g_step_graph_n; ++i)
+        if (g_step_graphs[i].key == key) {
+            g_step_graphs[i].used = ++g_step_graph_tick;
+            return cudaGraphLaunch(g_step_graphs[i].exec, s);
+        }
+    cudaStream_t& cap = g_capture_stream[key.dev];
+    if (!cap) {
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t e_enq = enqueue_per_depth<LT>(d, plan, slab, slow, taps, partials, z_begin, z_end, head,
+                                                    ws_slab, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    if (e_enq != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return e_enq != cudaSuccess ? e_enq : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    int slot = g_step_graph_n;
+    if (g_step_graph_n < 8) {
+        ++g_step_graph_n;
+    } else {
+        slot = 0;
+        for (int i = 1; i < 8; ++i)
+            if (g_step_graphs[i].used < g_step_graphs[slot].used) slot = i;
+        cudaGraphExecDestroy(g_step_graphs[slot].exec);
+    }
+    g_step_graphs[slot].key = key;
+    g_step_graphs[slot].exec = exec;
+    g_step_graphs[slot].used = ++g_step_graph_tick;
+    return cudaGraphLaunch(exec, s);
+}
+
+template <int LT>
+static cudaError_t enqueue_per_depth(const fxmig_desc* d, const MigratePlan& plan, void* slab, const float* slow,
+                                     const float4* taps, float* partials, int z_begin, int z_end, int* head,
+                                     float2* ws_slab, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     StepArgs a = {};
     a.nx = d->nx; a.nw = d->nw; a.nk = d->nk; a.G = plan.groups; a.i0 = d->i0; a.nt = d->nt;
     a.nxp = slow_pitch(d->nx);

@@ -1,5 +1,6 @@
 // t2f.cu -- time -> frequency transform of the zero-offset section
-// (Algorithm 1, "Fourier transform of shot gather along the t-axis"; Sec. III).
+// (Algorithm 1, the first step: each trace is taken from time to frequency;
+// Sec. III).
 //
 // Batched mixed-radix real FFT: two real traces a, b are packed as one complex
 // signal z = a + i b, transformed by an in-shared-memory Stockham autosort FFT

@@ -1,8 +1,8 @@
 """Sharding one migration over processes by frequency.
 
-Every frequency line is extrapolated independently through all depth steps
-(Sec. II: the extrapolation "can be performed independently for each
-frequency"), so ranks can own disjoint, contiguous blocks of the band with no
+Every frequency line is extrapolated through all depth steps without reference
+to any other frequency (Sec. II: the frequencies decouple in the f-x domain),
+so ranks can own disjoint, contiguous blocks of the band with no
 communication until the end; the only exchange is the image, the sum over
 frequencies (Algorithm 1), which is reduced here in rank order so that the
 result does not depend on the collective's internal order.
@@ -47,3 +47,46 @@ def reduce_images_rank_order(image, group=None):
     for p in parts[1:]:
         out += p
     return out
+
+
+def _migrate_on_device(sd, slab, vel, table, launch=None, stream=None):
+    """One rank's block through the library: the depth loop over all rows of
+    `sd` on the rank's lines, then its image (float32 [nz][nx], on the
+    slab's device)."""
+    import torch
+
+    import paper_1912_05529_gb300 as fx
+    dev = slab.device
+    partials = torch.empty((fx.fxmig_num_partials(sd, launch), sd.nz, sd.nx), dtype=torch.float32, device=dev)
+    ws = torch.zeros(fx.fxmig_workspace_bytes(sd, fx.FXMIG_WS_MIGRATE), dtype=torch.uint8, device=dev)
+    image = torch.empty((sd.nz, sd.nx), dtype=torch.float32, device=dev)
+    fx.fxmig_migrate_ex(sd, launch, slab, vel, table, partials, 0, sd.nz, ws, stream)
+    fx.fxmig_image(sd, partials, image, stream)
+    rc = fx.fxmig_check(ws, stream)
+    if rc != fx.FXMIG_OK:
+        raise fx.FxmigError(rc, "fxmig_migrate_ex (frequency shard)")
+    return image
+
+
+def migrate_frequency_shard(d, slab, vel, table, launch=None, group=None, stream=None, migrate_fn=None):
+    """Algorithm 1 over a frequency-sharded band: this rank migrates its
+    contiguous block of lines (frequency_block / shard_desc: same table range
+    k_max, first bin i0 + j0) and the images of all ranks are summed in rank
+    order on every rank.
+
+    slab       this rank's lines [j0, j0 + n) of the band, [n][nx] complex64
+               (device tensor; ignored when the block is empty)
+    vel, table the full velocity field and operator table (every rank)
+    migrate_fn (sd, slab, vel, table, launch, stream) -> image [nz][nx]; the
+               library by default
+    Returns the image of the whole band [nz][nx] (same on every rank)."""
+    import torch
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    sd = shard_desc(d, world, rank)
+    if sd is None:
+        dev = vel.device if hasattr(vel, "device") else "cpu"
+        image = torch.zeros((d.nz, d.nx), dtype=torch.float64 if migrate_fn else torch.float32, device=dev)
+    else:
+        image = (migrate_fn or _migrate_on_device)(sd, slab, vel, table, launch, stream)
+    return reduce_images_rank_order(image, group)

@@ -45,6 +45,44 @@ def desc_of(fx, w, k_max):
                    dt=w.dt, theta_max_deg=w.theta_deg, k_max=k_max)
 
 
+def max_abs_rel(a, b):
+    """max |a - b| over the largest |b| (a localised error, e.g. at a seam
+    between CTAs, that a global norm could hide)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    m = float(np.max(np.abs(b))) if b.size else 0.0
+    return float(np.max(np.abs(a - b)) / (m if m > 0 else 1.0)) if a.size else 0.0
+
+
+# per-element bars next to the norm bars: a slice element may deviate by 1e-4
+# of the slice's largest value (the norm bar allows 1e-5 on average), an image
+# pixel by 1e-3 of the image's largest value
+TOL_SLICE_MAX = 1e-4
+TOL_IMAGE_MAX = 1e-3
+
+
+def modeled_problem(w, noise=0.01):
+    """Parity input with dipping events: the layered lens model's reflectivity
+    taken up to the surface with the oracle's conjugate operators (oracle.model,
+    the exact adjoint of the depth loop: upward extrapolation with the
+    conjugate table operators), shaped by the Ricker spectrum (25 Hz), plus
+    complex Gaussian noise of `noise` times the data RMS (seeded)."""
+    v, refl = W.layered_lens_model(w)
+    vm = (0.5 * v).astype(np.float32)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    k_max = float(om[-1] / float(vm.min()))
+    table = O.design_operators(w.nk, k_max, w.dx, w.dz, w.L, w.theta_deg)
+    _, dk = O.k_grid(w.nk, k_max)
+    q = O.q_values(om, dk)
+    P0 = O.model(refl, vm, table, q)
+    f = (w.i0 + np.arange(w.nw)) / (w.nt * w.dt)
+    P0 = P0 * O.ricker_spectrum(f, 25.0, w.dt)[:, None]
+    rng = np.random.default_rng(w.seed + 1000)
+    rms = float(np.sqrt(np.mean(np.abs(P0) ** 2)))
+    P0 = P0 + noise * rms * (rng.standard_normal(P0.shape) + 1j * rng.standard_normal(P0.shape)) / math.sqrt(2)
+    return dict(vm=vm, k_max=k_max, table=table, q=q, P0=P0, refl=refl)
+
+
 def layered_inputs(w):
     v, refl = W.layered_lens_model(w)
     d = W.normal_incidence_section(w, v, refl)

@@ -10,7 +10,8 @@ import pytest
 
 import oracle as O
 import workloads as W
-from fxhelp import (TOL_DESIGN64, TOL_IMAGE, TOL_SLICE, TOL_T2F, desc_of, layered_inputs, problem, rel_l2,
+from fxhelp import (TOL_DESIGN64, TOL_IMAGE, TOL_IMAGE_MAX, TOL_SLICE, TOL_SLICE_MAX, TOL_T2F, desc_of, max_abs_rel,
+                    modeled_problem, layered_inputs, problem, rel_l2,
                     small_layered)
 
 pytestmark = pytest.mark.gpu
@@ -95,8 +96,7 @@ LAUNCHES = [None, dict(mode=1, cluster=1), dict(mode=1, cluster=2), dict(mode=1,
 @pytest.fixture(scope="module")
 def layered_case():
     w = small_layered()
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     chunks = [0, 1, 37, 80, w.nz]
@@ -115,9 +115,11 @@ def test_migrate_matches_oracle_per_depth_slice(fx, layered_case, launch):
     d = desc_of(fx, w, pr["k_max"])
     lc = fx.Launch(**launch) if launch else None
     slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, lc, chunks)
-    for s, r in zip(slabs, ref_slabs):
-        assert rel_l2(s, r) < TOL_SLICE
+    for s, r, ze in zip(slabs, ref_slabs, chunks[1:]):
+        assert rel_l2(s, r) < TOL_SLICE, ze
+        assert max_abs_rel(s, r) < TOL_SLICE_MAX, ze
     assert rel_l2(image, ref_image) < TOL_IMAGE
+    assert max_abs_rel(image, ref_image) < TOL_IMAGE_MAX
     assert np.all(np.isfinite(image))
 
 
@@ -131,11 +133,78 @@ def test_split_equals_unsplit_and_deterministic(fx, layered_case):
     assert np.array_equal(b_slabs[-1], c_slabs[-1]) and np.array_equal(b_img, c_img)
 
 
+def _tie_slowness(q, n):
+    """A slowness s (fp32) with fl32(q s) = n + 1/2 exactly and fl32(1/fl32(1/s))
+    = s (so the velocity fl32(1/s) maps back to s), searched around (n + 1/2)/q;
+    None if none is found within 64 ulps."""
+    q = np.float32(q)
+    s0 = np.float32((n + 0.5) / float(q))
+    cand = [s0]
+    up = dn = s0
+    for _ in range(64):
+        up = np.nextafter(up, np.float32(np.inf))
+        dn = np.nextafter(dn, np.float32(0))
+        cand += [up, dn]
+    for s in cand:
+        if np.float32(q * s) == np.float32(n + 0.5):
+            v = np.float32(np.float32(1) / s)
+            if np.float32(np.float32(1) / v) == s:
+                return s, v
+    return None
+
+
+def test_lookup_ties_match_oracle(fx):
+    # Velocities chosen so that, on one frequency line, fl32(q s) is exactly
+    # n + 1/2 at every trace (Sec. III nearest-entry lookup; round half to
+    # even).  Every table row holds distinct random taps, so a lookup that
+    # rounds a tie the other way (or takes the product in FP64) picks another
+    # row and moves the output far outside the bar.
+    nx, nz, nk, L = 96, 3, 256, 8
+    w = W.Workload("ties", nx=nx, dx=12.5, nt=256, dt=0.004, nz=nz, dz=5.0, f_lo=10.0, f_hi=40.0, L=L, seed=3)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    k_max = float(om[-1] / 700.0)
+    _, dk = O.k_grid(nk, k_max)
+    q = O.q_values(om, dk)
+    j = w.nw // 2
+    rng = np.random.default_rng(21)
+    vel = np.empty((nz, nx), np.float32)
+    exact_ties = fp64_differs = 0
+    for z in range(nz):
+        for x in range(nx):
+            for _ in range(1000):
+                n = int(rng.integers(4, int(q[j] * (1.0 / 700.0)) - 4))
+                r = _tie_slowness(q[j], n)
+                if r is not None:
+                    break
+            assert r is not None
+            s, v = r
+            vel[z, x] = v
+            exact_ties += 1
+            fp64_differs += int(np.rint(float(q[j]) * float(s)) != np.rint(np.float32(q[j] * s)))
+    s_all = O.slowness(vel)
+    idx = O.lookup_index(np.float32(q[j]), s_all, nk)
+    assert np.all(np.float32(q[j]) * s_all == np.floor(np.float32(q[j]) * s_all) + np.float32(0.5))
+    assert np.all(idx % 2 == 0)  # ties go to the even neighbour
+    table = (rng.standard_normal((nk, L + 1)) + 1j * rng.standard_normal((nk, L + 1))) * 0.1
+    table[:, 0] += 0.5
+    table32 = table.astype(np.complex64)
+    P0 = (rng.standard_normal((w.nw, nx)) + 1j * rng.standard_normal((w.nw, nx))).astype(np.complex64)
+    P_ref, img_ref = O.migrate(P0.astype(np.complex128), vel, table32.astype(np.complex128), q)
+    d = fx.Desc(nx=nx, nz=nz, nt=w.nt, nw=w.nw, i0=w.i0, L=L, nk=nk, dx=w.dx, dz=w.dz, dt=w.dt,
+                theta_max_deg=w.theta_deg, k_max=k_max)
+    for launch in (None, dict(mode=1, cluster=2, groups=w.nw), dict(mode=2)):
+        lc = fx.Launch(**launch) if launch else None
+        slabs, image = run_gpu_migrate(fx, d, P0, vel, table32, lc)
+        assert rel_l2(slabs[-1][j], P_ref[j]) < TOL_SLICE, launch
+        assert max_abs_rel(slabs[-1][j], P_ref[j]) < TOL_SLICE_MAX, launch
+        assert rel_l2(image, img_ref) < TOL_IMAGE, launch
+    print(f"{exact_ties} exact ties, {fp64_differs} of them where an FP64 product would round differently")
+
+
 @pytest.mark.parametrize("L", [4, 8, 17, 20])
 def test_other_filter_lengths(fx, L):
     w = small_layered(nx=300, nz=40, L=L, seed=9)
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     P, img = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
@@ -173,8 +242,7 @@ def test_migrate_widths_not_multiple_of_four(fx, nx, launch):
     # rows of nx % 4 != 0 floats are not 16-byte aligned in device memory:
     # the persistent form then converts velocity rows in shared memory
     w = small_layered(nx=nx, nz=30, name=f"layered_{nx}")
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
@@ -195,8 +263,7 @@ def test_cut_lines(fx, L, prec):
     # step behind and compute the L redundant outputs on the other side; odd
     # L, 16-bit storage, several depth ranges
     w = small_layered(nx=1000, nz=24, L=L, seed=11, name="layered_1000")
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
@@ -217,8 +284,7 @@ def test_cut_lines_tiny_halves(fx, nx, L, prec):
     # the redundant outputs (L) reach past the neighbour's half and past the
     # line ends, where the wavefield is zero.
     w = small_layered(nx=nx, nz=24, L=L, seed=17, name=f"layered_{nx}")
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
@@ -239,8 +305,7 @@ def test_cut_lines_straddling_warps(fx):
     # lines over clusters of 2: the segments of a CTA run across warp
     # boundaries and the cut falls at an odd chunk
     w = small_layered(nx=496, nz=20, L=12, seed=13, name="layered_496")
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     d = desc_of(fx, w, pr["k_max"])
@@ -249,3 +314,25 @@ def test_cut_lines_straddling_warps(fx):
     P_ref, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
     assert rel_l2(slabs[-1], P_ref) < TOL_SLICE
     assert rel_l2(image, img_ref) < TOL_IMAGE
+
+
+def test_frequency_shards_on_device_sum_to_full_band(fx):
+    # the ω-shard helper's per-rank path (shard_desc, the library's depth loop
+    # and imaging on the rank's lines) for every rank of a 3-way split, summed
+    # in rank order, against the full-band oracle
+    from paper_1912_05529_gb300 import distributed as D
+    w = small_layered(nx=300, nz=30, seed=23, name="layered_300")
+    pr = modeled_problem(w)
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    d = desc_of(fx, w, pr["k_max"])
+    _, img_ref = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
+    vel, table = _cuda(pr["vm"], torch.float32), _cuda(table32, torch.complex64)
+    total = torch.zeros((w.nz, w.nx), dtype=torch.float32, device="cuda")
+    for rank in range(3):
+        j0, n = D.frequency_block(w.nw, 3, rank)
+        sd = D.shard_desc(d, 3, rank)
+        assert sd.i0 == d.i0 + j0 and sd.nw == n and sd.k_max == d.k_max
+        total += D._migrate_on_device(sd, _cuda(P0_32[j0:j0 + n], torch.complex64), vel, table)
+    torch.cuda.synchronize()
+    assert rel_l2(total.cpu().numpy(), img_ref) < TOL_IMAGE

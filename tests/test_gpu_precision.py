@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from fxhelp import TOL_IMAGE, TOL_SLICE, desc_of, layered_inputs, problem, rel_l2, small_layered
+from fxhelp import TOL_IMAGE, TOL_SLICE, desc_of, layered_inputs, modeled_problem, problem, rel_l2, small_layered
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -57,8 +57,7 @@ MEETS_BAR = {"FP16_SPLIT"}
 @pytest.fixture(scope="module")
 def layered_case():
     w = small_layered()
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     table32 = pr["table"].astype(np.complex64)
     P0_32 = pr["P0"].astype(np.complex64)
     P, img = O.migrate(P0_32.astype(np.complex128), pr["vm"], table32.astype(np.complex128), pr["q"])
@@ -105,8 +104,7 @@ def test_multiwave_plan_matches_oracle(fx, oracle_mod):
     # 4096 traces x 401 frequencies, one line per cluster of 2 (half a line,
     # 256 chunks, per CTA): more CTAs than SMs, several waves
     w = W.Workload("wide", nx=4096, dx=12.5, nt=2000, dt=0.002, nz=6, dz=5.0, f_lo=5.0, f_hi=105.0, L=12, seed=9)
-    v, refl, sec = layered_inputs(w)
-    pr = problem(w, v, sec)
+    pr = modeled_problem(w)
     d = desc_of(fx, w, pr["k_max"])
     launch = fx.Launch(mode=1, cluster=2, groups=d.nw)
     assert fx.fxmig_launch_shape(d, launch).waves > 1

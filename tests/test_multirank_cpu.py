@@ -105,3 +105,53 @@ def test_two_rank_frequency_shard_equals_single_process():
         assert np.max(np.abs(total - full)) <= 1e-12 * np.max(np.abs(full))
     assert np.array_equal(res[0][1], res[1][1])       # every rank holds the same sum
     assert res[0][2] > 0 and math.isclose(res[1][2], 2 * res[0][2], rel_tol=1e-12)  # linear in the data
+
+
+def _shard_worker(rank, world, port, q):
+    # the library's shard helper with the oracle as the per-rank depth loop:
+    # the helper's bookkeeping (i0, nw, k_max of each block) and rank-order
+    # reduction against the full-band oracle
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    import oracle as O
+    import paper_1912_05529_gb300 as fx
+    from paper_1912_05529_gb300 import distributed as D
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, vm, table, qv, P0 = _problem()
+        d = fx.Desc(nx=w.nx, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz, dt=w.dt,
+                    theta_max_deg=w.theta_deg, k_max=float(O.omegas(w.i0, w.nw, w.nt, w.dt)[-1] / vm.min()))
+        j0, n = D.frequency_block(w.nw, world, rank)
+
+        def oracle_block(sd, slab, vel, tab, launch, stream):
+            om = O.omegas(sd.i0, sd.nw, sd.nt, sd.dt)
+            _, dk = O.k_grid(sd.nk, sd.k_max)
+            _, img = O.migrate(slab, vel, tab, O.q_values(om, dk))
+            return torch.from_numpy(img)
+
+        total = D.migrate_frequency_shard(d, P0[j0:j0 + n], vm, table, migrate_fn=oracle_block)
+        q.put((rank, total.numpy(), j0, n))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_helper_matches_full_band_oracle():
+    import oracle as O
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w, vm, table, qv, P0 = _problem()
+    _, full = O.migrate(P0, vm, table, qv)
+    assert [r[2] for r in res] == [0, res[0][3]] and sum(r[3] for r in res) == w.nw
+    for _, total, _, _ in res:
+        assert np.max(np.abs(total - full)) <= 1e-12 * np.max(np.abs(full))
+    assert np.array_equal(res[0][1], res[1][1])
