@@ -365,7 +365,7 @@ def measure_per_depth(fx, d, b, slab0, steps, flush):
     torch.cuda.synchronize()
     l2_gbs = 2.0 * nb * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
     return {"ms_per_step": float(np.mean(ms)), "migrate_ms": float(np.mean(mig)), "partials": nparts,
-            "kernels_per_step": 2 + d.nz, "graph": "the depth launches replayed as one CUDA graph",
+            "kernels_per_step": 4 + d.nz, "graph": "the depth launches replayed as one CUDA graph",
             "l2_copy_gbs": l2_gbs, "image": image.cpu().numpy()}
 
 
@@ -796,7 +796,7 @@ def run_batch(args):
         "e2e": {"value": e2e_val, "unit": "point*freq/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "includes": "H2D wavefields+velocities, batch depth loop, imaging, D2H images"},
-        "gpu_launches": (2 + len(bufs)) * args.steps,
+        "gpu_launches": (3 + len(bufs)) * args.steps,
         "clocks": clk.summary(),
         "compare": {
             "per_line_persistent": {"ms": t_persistent, "value": points / (t_persistent * 1e-3),
@@ -985,9 +985,10 @@ def run_native(args, w):
         "e2e": {"value": e2e_val, "unit": "point*freq/s",
                 "h2d_bytes_per_step": int(sec.nbytes + vm.nbytes), "d2h_bytes_per_step": int(d.nz * d.nx * 4),
                 "includes": "H2D section+velocity, t->f, depth loop, imaging, D2H image (table resident)"},
-        # per timed step: table expansion, slowness, depth loop, image (persistent);
-        # table expansion, one launch per depth row, image (per-depth form)
-        "gpu_launches": (4 if args.mode != 2 else 2 + d.nz) * args.steps,
+        # per timed step: table expansion, slowness, line norms (image scale),
+        # depth loop, image (persistent); the same with one launch per depth
+        # row (per-depth form)
+        "gpu_launches": (5 if args.mode != 2 else 4 + d.nz) * args.steps,
         "clocks": clk.summary(),
     }
     img_ref = None

@@ -156,10 +156,17 @@ __global__ void __launch_bounds__(256) k_batch_norms(const __grid_constant__ Bat
     __syncthreads();
     if (!last) return;
     __shared__ int e_sh;
+    __threadfence();
+    double Bt = 0.0;
+    for (int j = threadIdx.x; j < a.nw; j += blockDim.x) Bt = fmax(Bt, __ldcg(norms + j));
+    red[threadIdx.x] = Bt;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        __threadfence();
-        double B = 0.0;
-        for (int j = 0; j < a.nw; ++j) B = fmax(B, *((volatile const double*)(norms + j)));
+        const double B = red[0];
         int e = 0;
         if (B > 0.0 && B <= 1.0e300) {
             int k;

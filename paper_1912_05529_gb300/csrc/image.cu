@@ -27,13 +27,22 @@
 namespace fxmig_impl {
 
 // image[z][x] = acc[z][acc_slot(x)] * 2^-e[z]  (HBM-bound: 12 bytes per pixel;
-// a warp reads 32 consecutive pixels from 4 whole chunks)
+// a warp reads 32 consecutive pixels from 4 whole chunks).  The integer is
+// rounded to fp32 once (round to nearest) and scaled by an exact power of two,
+// so the pixel is the correctly rounded value of acc * 2^-e (outside the
+// subnormal range), without FP64 arithmetic.
+__device__ __forceinline__ float exp2_int(int e) {  // 2^e, e in [-149, 127]
+    return e >= -126 ? __int_as_float((e + 127) << 23) : __int_as_float(1 << (e + 149));
+}
 __global__ void __launch_bounds__(256) k_image_fixed(const long long* __restrict__ acc, const int* __restrict__ e,
                                                       int nz, int nx, int pitch, float* __restrict__ image) {
     const size_t n = (size_t)nz * nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int z = (int)(i / (size_t)nx), x = (int)(i - (size_t)z * nx);
-        image[i] = (float)ldexp((double)__ldcs(acc + (size_t)z * pitch + acc_slot(x)), -__ldg(e + z));
+        const float v = __ll2float_rn(__ldcs(acc + (size_t)z * pitch + acc_slot(x)));
+        // 2^-e in two factors when it alone would be subnormal or overflow
+        const int ez = -__ldg(e + z);
+        image[i] = (ez >= -126 && ez <= 127) ? v * exp2_int(ez) : (v * exp2_int(ez / 2)) * exp2_int(ez - ez / 2);
     }
 }
 
@@ -89,10 +98,19 @@ __global__ void __launch_bounds__(256) k_line_norms(const float2* __restrict__ s
     __syncthreads();
     if (!last) return;
     __shared__ int e_sh;
+    // the largest norm (the blocks' writes are visible: each fenced before
+    // its counter increment), a block-wide max in a fixed order
+    __threadfence();
+    double Bt = 0.0;
+    for (int j = threadIdx.x; j < nw; j += blockDim.x) Bt = fmax(Bt, __ldcg(norms + j));
+    red[threadIdx.x] = Bt;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        __threadfence();
-        double B = 0.0;
-        for (int j = 0; j < nw; ++j) B = fmax(B, *((volatile const double*)(norms + j)));
+        const double B = red[0];
         int e = 0;
         if (B > 0.0 && B <= 1.0e300) {
             int k;
