@@ -981,7 +981,8 @@ def run_native(args, w):
                      "traffic": kernel_traffic(w.name) if args.mode != 2 else None,
                      "kernel": "k_depth" if args.mode != 2 else "k_migrate_step",
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
-                     "ops_per_point": ops_per_point(w.L), "migrate_ms": mig_avg},
+                     "ops_per_point": ops_per_point(w.L), "migrate_ms": mig_avg,
+                     "image_ms": float(np.mean([b_ - a_ for a_, b_ in zip(mig_ms, step_ms)]))},
         "e2e": {"value": e2e_val, "unit": "point*freq/s",
                 "h2d_bytes_per_step": int(sec.nbytes + vm.nbytes), "d2h_bytes_per_step": int(d.nz * d.nx * 4),
                 "includes": "H2D section+velocity, t->f, depth loop, imaging, D2H image (table resident)"},
