@@ -299,7 +299,12 @@ __device__ __forceinline__ void depth_fir(const typename WS::T* __restrict__ cur
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const float2 a = f2_unpack(A[r]), b = f2_unpack(B[r]);
-        res[r] = (r < nv) ? f2_pack(a.x - b.y, a.y + b.x) : 0ull;
+        res[r] = f2_pack(a.x - b.y, a.y + b.x);
+    }
+    if (nv < 8) {  // the last chunk of a line: outputs beyond it stay zero
+#pragma unroll
+        for (int r = 1; r < 8; ++r)
+            if (r >= nv) res[r] = 0ull;
     }
     if (skip == 0u) {
         store8<LT, WS>(nxt + wb, res);
@@ -331,8 +336,17 @@ __device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict_
 __device__ __forceinline__ void depth_image_item(long long* __restrict__ dst, const u64 (&own)[8], int nv,
                                                  float scale, bool& over, uint32_t sw) {
     long long q[8];
+    (void)nv;  // own[r] is zero for r >= nv (outside the line), and so is its contribution
+    // rint(v * 2^e) as int32 (the conversion saturates beyond the range; one
+    // range check over the item flags it)
+    float m = 0.f;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) q[r] = r < nv ? image_fixed(f2_unpack(own[r]).x, scale, over) : 0;
+    for (int r = 0; r < 8; ++r) {
+        const float t = f2_unpack(own[r]).x * scale;
+        m = fmaxf(m, fabsf(t));
+        q[r] = (long long)__float2int_rn(t);
+    }
+    if (!(m < kImageFixedMax)) over = true;
 #pragma unroll
     for (int p = 0; p < 4; ++p)
         *reinterpret_cast<longlong2*>(dst + 2 * (p ^ sw)) = make_longlong2(q[2 * p], q[2 * p + 1]);
