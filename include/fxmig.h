@@ -60,7 +60,12 @@ extern "C" {
 /* Migration forms for fxmig_launch.mode. */
 #define FXMIG_MODE_AUTO       0
 #define FXMIG_MODE_PERSISTENT 1  /* one launch; each frequency line stays in shared memory for all depths */
-#define FXMIG_MODE_PER_DEPTH  2  /* one launch per depth step; the wavefield streams through L2/HBM */
+#define FXMIG_MODE_PER_DEPTH  2  /* one launch per depth step; the wavefield streams through L2/HBM.
+                                   The launches of a call are captured once into a CUDA graph per
+                                   argument set (kept per process, a few at a time) and replayed;
+                                   inside a stream capture they are launched directly.  After
+                                   cudaDeviceReset the kept graphs are stale: do not call this
+                                   form again on that device. */
 
 /* Storage precision of the persistent form (fxmig_launch.precision).  The
  * arithmetic is FP32 in every form (packed f32x2 multiply-adds); what
