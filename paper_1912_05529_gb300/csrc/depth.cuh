@@ -155,7 +155,7 @@ __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int
     L.off_img = align16(o);
     o = L.off_img + 2 * (size_t)L.nchunks * 8 * 8;  // fixed-point image rows [2][chunks][8] int64
     L.off_queue = align16(o);
-    o = L.off_queue + (fixq ? 16 + (size_t)L.nchunks * 7 * 8 : 0);  // count, entries (position | r, operator)
+    o = L.off_queue + (fixq ? 16 + (size_t)L.nchunks * 7 * 8 : 0);  // counts and claim heads [parity], entries
     L.off_wave = align16(o);
     L.total = L.off_wave + 2 * (size_t)elems * esize;
     return true;
@@ -185,8 +185,8 @@ __device__ __forceinline__ int depth_op_index(float q, float v, int nk) {
     else return table_index(q, v, nk);
 }
 
-// Warm the operator row tp[0..LT] into L1 (rows of operator changes, read by
-// the fixup round after the main items).
+// Warm the operator row tp[0..LT] into L1 (the halo warp's redundant output,
+// whose operator is known a step before its FIR).
 template <int LT, class TP>
 __device__ __forceinline__ void depth_prefetch_taps(const typename TP::E* tp) {
     constexpr int kBytes = (LT + 1) * (int)sizeof(typename TP::E);
@@ -213,10 +213,12 @@ __device__ __forceinline__ u64 depth_stored(u64 v) {
 // srow): idx0, the operator of its first point, which all 8 outputs use in
 // the main FIR; the returned mask flags the outputs (r < nv) whose own
 // operator differs (recomputed separately), idx1 their common operator (or
-// -1).  The flagged operators' tap rows are prefetched into L1.
-template <int LT, class TP, bool kPairs>
-__device__ __forceinline__ uint32_t depth_ops(const float* __restrict__ srow, float q, int nk, int nv,
-                                              const typename TP::E* __restrict__ taps, int& idx0, int& idx1) {
+// -1).  (The flagged operators' tap rows are not prefetched: every lane of
+// every compute warp would issue its own prefetches at the start of the step,
+// and the flood of L1 requests costs more than the later loads it saves.)
+template <bool kPairs>
+__device__ __forceinline__ uint32_t depth_ops(const float* __restrict__ srow, float q, int nk, int nv, int& idx0,
+                                              int& idx1) {
     float s8[8];
     load_s8(srow, s8);
     idx0 = depth_op_index<kPairs>(q, s8[0], nk);
@@ -234,7 +236,6 @@ __device__ __forceinline__ uint32_t depth_ops(const float* __restrict__ srow, fl
             if (r < nv && idx != idx0) {
                 uni &= (mask == 0u) || (idx == last);
                 mask |= 1u << r;
-                if (idx != last) depth_prefetch_taps<LT, TP>(taps + (size_t)idx * (LT + 1));
                 last = idx;
             }
         }
@@ -324,7 +325,7 @@ __device__ __forceinline__ uint32_t depth_item(const typename WS::T* __restrict_
                                                uint32_t wb, const float* __restrict__ srow, float q, int nk, int nv,
                                                const typename TP::E* __restrict__ taps, u64 (&own)[8], int& idx1) {
     int idx0;
-    const uint32_t mask = depth_ops<LT, TP, kPairs>(srow, q, nk, nv, taps, idx0, idx1);
+    const uint32_t mask = depth_ops<kPairs>(srow, q, nk, nv, idx0, idx1);
     depth_fir<LT, WS, TP>(cur, nxt, wb, idx0, nv, taps, own, 0u);
     return mask;
 }
@@ -419,6 +420,30 @@ __device__ __forceinline__ void depth_fixups(uint32_t mask, uint32_t wb, uint32_
     }
 }
 
+// Drain of the operator-change queue of one step by one warp: n entries
+// (position | r << 28, operator) in queue[0, n); the warps that drain it
+// claim 32 entries at a time from the shared head counter, one single-output
+// FIR per lane, until none are left.  n is uniform over the warp.
+template <int LT, class WS, class TP>
+__device__ __forceinline__ void depth_drain(const uint2* __restrict__ queue, int* head, int n,
+                                            const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
+                                            const typename TP::E* __restrict__ taps, int lane) {
+    if (n <= 0) return;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(head, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const int i = base + lane;
+        if (i < n) {
+            const uint2 e = queue[i];
+            const uint32_t wbo = e.x & 0x0fffffffu;
+            const int r = (int)(e.x >> 28);
+            WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)e.y * (LT + 1)));
+        }
+    }
+}
+
 __device__ __forceinline__ void depth_mbar_arrive_remote(uint32_t remote_bar) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(remote_bar) : "memory");
 }
@@ -464,9 +489,12 @@ __device__ __forceinline__ void depth_mbar_arrive(uint64_t* bar) {
 // With a fixup warp (fixw), the compute warps do not recompute the outputs
 // whose operator differs from their item's: each lane queues them (position,
 // operator) right after its operator analysis, the warp arrives on the queue
-// barrier, and the fixup warp computes them (single-output FIRs) while the
-// compute warps run their main FIRs, which leave those outputs unwritten.
-// The lanes reload them into their registers after the step barrier.
+// barrier, and the fixup warp starts computing them (single-output FIRs)
+// while the compute warps run their main FIRs, which leave those outputs
+// unwritten; a compute warp that finds entries in the queue after its main
+// FIR joins the drain, so the queue's tail is spread over the warps that
+// finish first.  The lanes reload the queued outputs into their registers
+// after the step barrier.
 template <int LT, class WS, class TP, int NR, bool kPairs>
 __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
@@ -497,6 +525,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
     uint64_t* inbar = mbar + kDepthRowSlots;  // [parity]
     uint64_t* qbar = mbar + kDepthRowSlots + 2;
     int* hstop = reinterpret_cast<int*>(smem + L.off_prog);  // cut: the neighbour gave up the exchange
+    // operator-change queue: entry counts [parity], claim heads [parity]
     int* qcount = reinterpret_cast<int*>(smem + L.off_queue);
     uint2* queue = reinterpret_cast<uint2*>(smem + L.off_queue + 16);
     float* qs = reinterpret_cast<float*>(smem + L.off_qs);
@@ -517,7 +546,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
         for (int b = 0; b < 2; ++b) mbar_init(&inbar[b], 1);  // the local expect_tx arrival (plus the bytes)
         mbar_init(qbar, (uint32_t)a.ncw);                      // every compute warp, once per step
         *hstop = 0;
-        if (kFixW) *qcount = 0;
+        if (kFixW) qcount[0] = qcount[1] = qcount[2] = qcount[3] = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -610,7 +639,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
             for (int r = 0; r < 8; ++r) own[k][r] = nv[k] > 0 ? WS::ld1(wave + wb[k] + phys(r + LT)) : 0ull;
         }
         bool over = false;
-        uint32_t pend[NR];  // outputs the fixup warp wrote in the last step
+        bool qok = true;
+        uint32_t pend[NR];  // outputs the queue's drainers wrote in the last step
 #pragma unroll
         for (int k = 0; k < NR; ++k) pend[k] = 0u;
         for (int t = 0; t < nsteps; ++t) {
@@ -631,7 +661,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     if constexpr (kPairs) qz[k] = __int_as_float(ln[k] * a.pair_cnt[z]);
                     int i1;
                     idx0[k] = 0;
-                    mk[k] = nv[k] > 0 ? depth_ops<LT, TP, kPairs>(row + ro[k], qz[k], a.nk, nv[k], taps, idx0[k], i1)
+                    mk[k] = nv[k] > 0 ? depth_ops<kPairs>(row + ro[k], qz[k], a.nk, nv[k], idx0[k], i1)
                                       : 0u;
                     cnt += __popc(mk[k]);
                 }
@@ -645,7 +675,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     }
                     const int total = __shfl_sync(0xffffffffu, incl, 31);
                     int base = 0;
-                    if (lane == 31) base = atomicAdd(qcount, total);
+                    if (lane == 31) base = atomicAdd(&qcount[t & 1], total);
                     int pos = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
 #pragma unroll
                     for (int k = 0; k < NR; ++k)
@@ -676,6 +706,16 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 for (int k = 0; k < NR; ++k) {
                     if (nv[k] > 0) depth_fir<LT, WS, TP>(cur, nxt, wb[k], idx0[k], nv[k], taps, own[k], mk[k]);
                     pend[k] = mk[k];
+                }
+                // then help drain the step's queue, if it has entries (a
+                // glance at the count, which only grows during the step; the
+                // fixup warp drains whatever the compute warps leave)
+                const int qseen = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&qcount[t & 1]), 0);
+                if (qok && qseen > 0) {
+                    qok = __all_sync(0xffffffffu, mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls));
+                    if (!qok && lane == 0) atomicOr(a.status, kStatusTimeout);
+                    const int nq = __shfl_sync(0xffffffffu, qok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
+                    depth_drain<LT, WS, TP>(queue, &qcount[2 + (t & 1)], nq, cur, nxt, taps, lane);
                 }
             } else {
 #pragma unroll
@@ -712,7 +752,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
         }
         if (over) atomicOr(a.status, kStatusOverflow);
     } else if (fix_warp) {
-        // ---- the fixup warp (queued outputs; row staging and image hand-off)
+        // ---- the fixup warp (drains the queue with the compute warps that
+        // join; row staging, image hand-off, the queue counters)
         bool ok = true;
         for (int t = 0; t < nsteps; ++t) {
             const T* cur = wave + (size_t)(t & 1) * buf;
@@ -722,19 +763,15 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 if (t + kDepthRowSlots - 1 < nsteps) issue_row(t + kDepthRowSlots - 1);
                 if (t + 1 < nsteps) wait_row(t + 1);
             }
-            if (ok && !mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls)) {
-                ok = false;
-                if (lane == 0) atomicOr(a.status, kStatusTimeout);
+            // the counters of step t + 1 (last used in step t - 1, whose
+            // drainers all passed the last barrier)
+            if (lane == 0) qcount[(t + 1) & 1] = qcount[2 + ((t + 1) & 1)] = 0;
+            if (ok) {
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls));
+                if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
-            const int n = ok ? *reinterpret_cast<volatile int*>(qcount) : 0;
-            for (int i = lane; i < n; i += 32) {
-                const uint2 e = queue[i];
-                const uint32_t wbo = e.x & 0x0fffffffu;
-                const int r = (int)(e.x >> 28);
-                WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)e.y * (LT + 1)));
-            }
-            __syncwarp();
-            if (lane == 0) *qcount = 0;
+            const int n = __shfl_sync(0xffffffffu, ok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
+            depth_drain<LT, WS, TP>(queue, &qcount[2 + (t & 1)], n, cur, nxt, taps, lane);
             if (duty) depth_bulk_wait_read();
             step_barrier();
             if (duty) issue_image(t);
