@@ -866,6 +866,9 @@ def measure_batch_form(fx, flush, steps: int = 3, warmup: int = 3, oracle_check:
 
 
 # ------------------------------------------------------------------ GPU leg
+FORM_NAMES = ("learned", "precision", "per_depth", "large", "batch")
+
+
 def run_native(args, w):
     import torch
     import torch.distributed as dist
@@ -952,18 +955,24 @@ def run_native(args, w):
 
     learned, precs, per_depth, large, batched = None, {}, None, {}, None
     oracle_leg = not args.no_cpu_baseline and world == 1
-    if world == 1 and not args.no_forms:
-        if d.L <= 15:
+    forms = set() if args.no_forms else {f.strip() for f in args.forms.split(",") if f.strip()}
+    if forms - set(FORM_NAMES):
+        raise SystemExit(f"unknown forms: {sorted(forms - set(FORM_NAMES))}")
+    if world == 1:
+        if "learned" in forms and d.L <= 15:
             learned = measure_learned(fx, d, b, slab0, args.steps, flush, train_steps=args.train_steps)
-        for name in PREC_NAMES:
-            precs[name] = measure_precision(fx, d, b, slab0, args.steps, flush, launch,
-                                            getattr(fx, "FXMIG_PREC_" + name))
-        if args.mode != 2:
+        if "precision" in forms:
+            for name in PREC_NAMES:
+                precs[name] = measure_precision(fx, d, b, slab0, args.steps, flush, launch,
+                                                getattr(fx, "FXMIG_PREC_" + name))
+        if "per_depth" in forms and args.mode != 2:
             per_depth = measure_per_depth(fx, d, b, slab0, min(args.steps, 5), flush)
         if w.name == "layered_lens_2048":
             # the 8192-trace line and the 64 uneven lines, recorded with this line
-            large = measure_large(fx, flush, oracle_check=oracle_leg)
-            batched = measure_batch_form(fx, flush, oracle_check=oracle_leg)
+            if "large" in forms:
+                large = measure_large(fx, flush, oracle_check=oracle_leg)
+            if "batch" in forms:
+                batched = measure_batch_form(fx, flush, oracle_check=oracle_leg)
 
     if rank != 0:
         if world > 1:
@@ -1090,7 +1099,10 @@ def main(argv=None):
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent form: 1, 2, or 0 (auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the learned-operator form")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other forms (learned operators, 16-bit "
+                    "storage, per-depth launches, the 8192-trace line, the 64-line batch)")
+    ap.add_argument("--forms", default=",".join(FORM_NAMES),
+                    help="comma-separated subset of the other forms to run: " + ", ".join(FORM_NAMES))
     ap.add_argument("--train-steps", type=int, default=100000, help="Adam steps of the operator network")
     ap.add_argument("--ref-freqs", type=int, default=24, help="frequencies per oracle step (reference arm)")
     args = ap.parse_args(argv)
