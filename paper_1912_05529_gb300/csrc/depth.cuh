@@ -495,16 +495,17 @@ __device__ __forceinline__ void depth_mbar_arrive(uint64_t* bar) {
 // FIR joins the drain, so the queue's tail is spread over the warps that
 // finish first.  The lanes reload the queued outputs into their registers
 // after the step barrier.
-template <int LT, class WS, class TP, int NR, bool kPairs>
+template <int LT, class WS, class TP, int NR, bool kPairs, bool kFQ = (NR == 1)>
 __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
     const typename TP::E* __restrict__ taps_all = static_cast<const typename TP::E*>(a.taps);
     const int C = a.C;
     const int rank = C > 1 ? (int)cluster_ctarank() : 0;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    // one item per lane: outputs with a different operator go to the fixup
-    // warp; two items per lane: recomputed in the warp (no room for a queue)
-    constexpr bool kFixW = NR == 1;
+    // kFQ: outputs with a different operator go to the fixup warp's queue
+    // (one item per lane always; two items per lane where the queue fits in
+    // shared memory), else the warp recomputes them in cooperative rounds
+    constexpr bool kFixW = kFQ;
     if (kFixW != (a.fixw != 0)) {  // launch inconsistent with the compiled form (uniform: no barrier reached)
         if (threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
         return;
@@ -690,7 +691,10 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 __syncwarp();
                 if (lane == 0) depth_mbar_arrive(qbar);
                 // image row z from the step's input values (the outputs the
-                // fixup warp wrote in the last step reloaded first)
+                // queue's drainers wrote in the last step reloaded first) and
+                // the main FIRs; with two items, item by item (the second
+                // item's image stores overlap the first one's FMAs on other
+                // warps)
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (pend[k]) {
@@ -701,11 +705,14 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     if (nv[k] > 0)
                         depth_image_item(img + (size_t)(t & 1) * nchunks * 8 + ((k * a.ncw + warp) * 32 + lane) * 8,
                                          own[k], nv[k], scale, over, sw[k]);
+                    if constexpr (NR > 1) {
+                        if (nv[k] > 0) depth_fir<LT, WS, TP>(cur, nxt, wb[k], idx0[k], nv[k], taps, own[k], mk[k]);
+                        pend[k] = mk[k];
+                    }
                 }
-#pragma unroll
-                for (int k = 0; k < NR; ++k) {
-                    if (nv[k] > 0) depth_fir<LT, WS, TP>(cur, nxt, wb[k], idx0[k], nv[k], taps, own[k], mk[k]);
-                    pend[k] = mk[k];
+                if constexpr (NR == 1) {
+                    if (nv[0] > 0) depth_fir<LT, WS, TP>(cur, nxt, wb[0], idx0[0], nv[0], taps, own[0], mk[0]);
+                    pend[0] = mk[0];
                 }
                 // then help drain the step's queue, if it has entries (a
                 // glance at the count, which only grows during the step; the
@@ -1098,18 +1105,18 @@ struct DepthWarps {
     static constexpr int kThreads = OCC == 1 ? (kMaxCompute + 2) * 32 : kMaxCompute * 32;
 };
 
-template <int LT, class WS, class TP, int NR, bool kPairs = false, int OCC = 1>
+template <int LT, class WS, class TP, int NR, bool kPairs = false, int OCC = 1, bool kFQ = (NR == 1)>
 __global__ void __launch_bounds__(DepthWarps<NR, OCC>::kThreads, OCC) k_depth(const DepthArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if constexpr (OCC == 2) run_depth_warps<LT, WS, TP, kPairs>(a, (int)blockIdx.x, smem);
-    else run_depth<LT, WS, TP, NR, kPairs>(a, (int)(blockIdx.x / a.C), smem);
+    else run_depth<LT, WS, TP, NR, kPairs, kFQ>(a, (int)(blockIdx.x / a.C), smem);
 }
 
 // Launch of the depth loop for a plan (plan_depth): the kernel compiled for
 // the plan's items per lane and CTAs per SM, clusters of plan.cluster CTAs.
-template <int LT, class WS, class TP, int NR, bool kPairs, int OCC>
+template <int LT, class WS, class TP, int NR, bool kPairs, int OCC, bool kFQ = (NR == 1)>
 inline cudaError_t launch_depth_nr(const MigratePlan& plan, const DepthArgs& a, cudaStream_t s) {
-    auto kern = k_depth<LT, WS, TP, NR, kPairs, OCC>;
+    auto kern = k_depth<LT, WS, TP, NR, kPairs, OCC, kFQ>;
     cudaError_t e = ensure_smem(kern, plan.smem, false);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -1134,7 +1141,9 @@ inline cudaError_t launch_depth(const MigratePlan& plan, const DepthArgs& a, cud
         return launch_depth_nr<LT, WS, TP, 1, kPairs, 2>(plan, a, s);
     }
     if (plan.nr == 1) return launch_depth_nr<LT, WS, TP, 1, kPairs, 1>(plan, a, s);
-    if (plan.nr == 2) return launch_depth_nr<LT, WS, TP, 2, kPairs, 1>(plan, a, s);
+    if (plan.nr == 2)
+        return plan.fixw ? launch_depth_nr<LT, WS, TP, 2, kPairs, 1, true>(plan, a, s)
+                         : launch_depth_nr<LT, WS, TP, 2, kPairs, 1, false>(plan, a, s);
     return cudaErrorInvalidValue;
 }
 

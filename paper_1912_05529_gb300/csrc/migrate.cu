@@ -285,9 +285,10 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
                     nr = 0;
                 }
             }
-            // one item per lane (one CTA per SM): a fixup warp and its queue
+            // one CTA per SM: a fixup warp and its queue (one item per lane:
+            // required; two: where the queue fits, else the in-warp rounds)
             int fixw = 0;
-            if (nr == 1 && occ == 1) {
+            if (occ == 1 && (nr == 1 || nr == 2)) {
                 size_t sf = 0;
                 for (int g = 0; g < G; ++g)
                     for (int r = 0; r < C; ++r) {
@@ -297,7 +298,7 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
                 if (sf <= smax) {
                     fixw = 1;
                     smem = sf;
-                } else {
+                } else if (nr == 1) {
                     nr = 0;
                 }
             }

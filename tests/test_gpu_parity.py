@@ -201,6 +201,45 @@ def test_lookup_ties_match_oracle(fx):
     print(f"{exact_ties} exact ties, {fp64_differs} of them where an FP64 product would round differently")
 
 
+@pytest.mark.parametrize("launch", [None, dict(mode=1, cluster=2), dict(mode=1, cluster=1),
+                                    dict(mode=1, cluster=2, groups=15, warps=6), dict(mode=1, ctas_per_sm=2)])
+def test_rough_velocity_every_output_queued(fx, launch):
+    # A velocity drawn independently at every point (Sec. III: each point
+    # takes its own table operator), so almost every output's operator differs
+    # from its 8-point item's first one: the persistent form queues up to 7 of
+    # every 8 outputs per step, and the queue is drained in many rounds by the
+    # fixup warp and the compute warps that join it.  Every slice and the image
+    # must still match the oracle.
+    w = W.Workload("rough_700", nx=700, dx=12.5, nt=512, dt=0.004, nz=40, dz=5.0, f_lo=5.0, f_hi=60.0, L=12,
+                   seed=8)
+    rng = np.random.default_rng(8)
+    v = rng.uniform(1500.0, 4000.0, size=(w.nz, w.nx)).astype(np.float32)
+    section = rng.standard_normal((w.nx, w.nt)).astype(np.float32)
+    pr = problem(w, v, section)
+    s_all = O.slowness(pr["vm"])
+    j = w.nw - 1
+    idx = O.lookup_index(np.float32(pr["q"][j]), s_all, w.nk)
+    first = np.repeat(idx[:, ::8], 8, axis=1)[:, : w.nx]
+    assert np.mean(idx != first) > 0.75  # most outputs of the top line leave their item's operator
+    table32 = pr["table"].astype(np.complex64)
+    P0_32 = pr["P0"].astype(np.complex64)
+    chunks = [0, 13, w.nz]
+    ref_slabs, ref_image = [], np.zeros((w.nz, w.nx))
+    P = P0_32.astype(np.complex128)
+    for zb, ze in zip(chunks[:-1], chunks[1:]):
+        P, img = O.migrate(P, pr["vm"], table32.astype(np.complex128), pr["q"], zb, ze)
+        ref_slabs.append(P.copy())
+        ref_image[zb:ze] = img[zb:ze]
+    d = desc_of(fx, w, pr["k_max"])
+    lc = fx.Launch(**launch) if launch else None
+    slabs, image = run_gpu_migrate(fx, d, P0_32, pr["vm"], table32, lc, chunks)
+    for sl, r, ze in zip(slabs, ref_slabs, chunks[1:]):
+        assert rel_l2(sl, r) < TOL_SLICE, ze
+        assert max_abs_rel(sl, r) < TOL_SLICE_MAX, ze
+    assert rel_l2(image, ref_image) < TOL_IMAGE
+    assert max_abs_rel(image, ref_image) < TOL_IMAGE_MAX
+
+
 @pytest.mark.parametrize("L", [4, 8, 17, 20])
 def test_other_filter_lengths(fx, L):
     w = small_layered(nx=300, nz=40, L=L, seed=9)
