@@ -421,13 +421,17 @@ __device__ __forceinline__ void depth_fixups(uint32_t mask, uint32_t wb, uint32_
 }
 
 // Drain of the operator-change queue of one step by one warp: n entries
-// (position | r << 28, operator) in queue[0, n); the warps that drain it
-// claim 32 entries at a time from the shared head counter, one single-output
-// FIR per lane, until none are left.  n is uniform over the warp.
-template <int LT, class WS, class TP>
+// (window base | segment << 16 | r << 28, slowness value of the output) in
+// queue[0, n); the warps that drain it claim 32 entries at a time from the
+// shared head counter and take the output's operator (its segment's line
+// factor qs[segment], or with kPairs the pair offset of the segment's line,
+// line * pc) and one single-output FIR per lane, until none are left.  n is
+// uniform over the warp.
+template <int LT, class WS, class TP, bool kPairs>
 __device__ __forceinline__ void depth_drain(const uint2* __restrict__ queue, int* head, int n,
                                             const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
-                                            const typename TP::E* __restrict__ taps, int lane) {
+                                            const typename TP::E* __restrict__ taps, const float* __restrict__ qs,
+                                            const DepthSeg* __restrict__ segs, int pc, int nk, int lane) {
     if (n <= 0) return;
     for (;;) {
         int base = 0;
@@ -437,9 +441,13 @@ __device__ __forceinline__ void depth_drain(const uint2* __restrict__ queue, int
         const int i = base + lane;
         if (i < n) {
             const uint2 e = queue[i];
-            const uint32_t wbo = e.x & 0x0fffffffu;
-            const int r = (int)(e.x >> 28);
-            WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)e.y * (LT + 1)));
+            const uint32_t wbo = e.x & 0xffffu;
+            const int sg = (int)((e.x >> 16) & 7u), r = (int)(e.x >> 28);
+            float q;
+            if constexpr (kPairs) q = __int_as_float(segs[sg].line * pc);
+            else q = qs[sg];
+            const int idx = depth_op_index<kPairs>(q, __uint_as_float(e.y), nk);
+            WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)idx * (LT + 1)));
         }
     }
 }
@@ -612,13 +620,13 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
 
     if (compute) {
         // ---- the lane's items (the same chunks at every step)
-        uint32_t wb[NR], ro[NR], sw[NR];
+        uint32_t wb[NR], ro[NR], sw[NR], sg[NR];
         float qv[NR];
         int nv[NR], ln[NR];
         u64 own[NR][8];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            wb[k] = ro[k] = sw[k] = 0u;
+            wb[k] = ro[k] = sw[k] = sg[k] = 0u;
             qv[k] = 0.f;
             nv[k] = 0;
             ln[k] = 0;
@@ -629,6 +637,7 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 const int c = item - segs[s].flat;
                 const int xg = segs[s].x0 + 8 * c;
                 wb[k] = (uint32_t)(segs[s].lbase + 10 * c);
+                sg[k] = (uint32_t)s;
                 ro[k] = (uint32_t)(xg - L.sx0);
                 sw[k] = (uint32_t)(xg >> 4) & 3u;
                 ln[k] = segs[s].line;
@@ -660,10 +669,9 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 for (int k = 0; k < NR; ++k) {
                     qz[k] = qv[k];
                     if constexpr (kPairs) qz[k] = __int_as_float(ln[k] * a.pair_cnt[z]);
-                    int i1;
                     idx0[k] = 0;
-                    mk[k] = nv[k] > 0 ? depth_ops<kPairs>(row + ro[k], qz[k], a.nk, nv[k], idx0[k], i1)
-                                      : 0u;
+                    int i1;
+                    mk[k] = nv[k] > 0 ? depth_ops<kPairs>(row + ro[k], qz[k], a.nk, nv[k], idx0[k], i1) : 0u;
                     cnt += __popc(mk[k]);
                 }
                 // queue the flagged outputs: one shared-memory atomic per warp
@@ -684,8 +692,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
 #pragma unroll
                             for (int r = 1; r < 8; ++r)
                                 if ((mk[k] >> r) & 1u)
-                                    queue[pos++] = make_uint2(wb[k] | ((uint32_t)r << 28),
-                                                              (uint32_t)depth_op_index<kPairs>(qz[k], row[ro[k] + r], a.nk));
+                                    queue[pos++] = make_uint2(wb[k] | (sg[k] << 16) | ((uint32_t)r << 28),
+                                                              __float_as_uint(row[ro[k] + r]));
                         }
                 }
                 __syncwarp();
@@ -722,7 +730,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     qok = __all_sync(0xffffffffu, mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls));
                     if (!qok && lane == 0) atomicOr(a.status, kStatusTimeout);
                     const int nq = __shfl_sync(0xffffffffu, qok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
-                    depth_drain<LT, WS, TP>(queue, &qcount[2 + (t & 1)], nq, cur, nxt, taps, lane);
+                    depth_drain<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], nq, cur, nxt, taps, qs, segs,
+                                                    kPairs ? a.pair_cnt[z] : 0, a.nk, lane);
                 }
             } else {
 #pragma unroll
@@ -778,7 +787,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             const int n = __shfl_sync(0xffffffffu, ok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
-            depth_drain<LT, WS, TP>(queue, &qcount[2 + (t & 1)], n, cur, nxt, taps, lane);
+            depth_drain<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], n, cur, nxt, taps, qs, segs,
+                                            kPairs ? a.pair_cnt[a.z_begin + t] : 0, a.nk, lane);
             if (duty) depth_bulk_wait_read();
             step_barrier();
             if (duty) issue_image(t);

@@ -290,12 +290,15 @@ int plan_depth(const fxmig_desc* d, int LT, int esize, int req_c, int req_g, int
             int fixw = 0;
             if (occ == 1 && (nr == 1 || nr == 2)) {
                 size_t sf = 0;
+                int bufmax = 0;
                 for (int g = 0; g < G; ++g)
                     for (int r = 0; r < C; ++r) {
                         depth_layout(d->nx, nxp, d->nw, G, C, g, r, LT, esize, L, false, true);
                         sf = std::max(sf, L.total);
+                        bufmax = std::max(bufmax, L.buf);
                     }
-                if (sf <= smax) {
+                // queue entries hold a window base in 16 bits
+                if (sf <= smax && bufmax < 65536) {
                     fixw = 1;
                     smem = sf;
                 } else if (nr == 1) {
