@@ -87,8 +87,9 @@ __host__ __device__ inline int depth_ceil8(int v) { return (v + 7) & ~7; }
 // windows start on 8-value blocks and the halo 2L fits), and 2L positions
 // right of its last chunk.  lane_rows: slowness staged per lane (the
 // decoupled form: kDepthLaneRowSlots slots of 8 values per chunk) instead of
-// whole row ranges.  fixq: a queue of the outputs whose operator differs from
-// their item's (8 bytes each, at most 7 per chunk) for the fixup warp.
+// whole row ranges.  fixq: a queue of the items with outputs whose operator
+// differs from their item's (8 bytes each, at most one per chunk) for the
+// fixup warp.
 // Returns false if the CTA would hold more than kDepthMaxSegs segments or
 // more than one cut.
 __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int C, int g, int rank, int LT,
@@ -155,7 +156,7 @@ __host__ __device__ inline bool depth_layout(int nx, int nxp, int nw, int G, int
     L.off_img = align16(o);
     o = L.off_img + 2 * (size_t)L.nchunks * 8 * 8;  // fixed-point image rows [2][chunks][8] int64
     L.off_queue = align16(o);
-    o = L.off_queue + (fixq ? 16 + (size_t)L.nchunks * 7 * 8 : 0);  // counts and claim heads [parity], entries
+    o = L.off_queue + (fixq ? 16 + (size_t)L.nchunks * 8 : 0);  // counts and claim heads [parity], entries
     L.off_wave = align16(o);
     L.total = L.off_wave + 2 * (size_t)elems * esize;
     return true;
@@ -420,34 +421,40 @@ __device__ __forceinline__ void depth_fixups(uint32_t mask, uint32_t wb, uint32_
     }
 }
 
-// Drain of the operator-change queue of one step by one warp: n entries
-// (window base | segment << 16 | r << 28, slowness value of the output) in
-// queue[0, n); the warps that drain it claim 32 entries at a time from the
-// shared head counter and take the output's operator (its segment's line
-// factor qs[segment], or with kPairs the pair offset of the segment's line,
-// line * pc) and one single-output FIR per lane, until none are left.  n is
-// uniform over the warp.
+// Drain of the operator-change queue of one step by one warp: n entries, one
+// per item with flagged outputs (window base | segment << 16 | flags >> 1 <<
+// 19, the item's offset in the staged slowness row) in queue[0, n); the
+// warps that drain it claim 4 items at a time from the shared head counter,
+// 8 lanes per item, lane r taking output r if it is flagged: its operator
+// from its slowness in the step's row and its segment's line factor
+// qs[segment] (with kPairs the pair offset of the segment's line, line *
+// pc), and one single-output FIR.  n is uniform over the warp.
 template <int LT, class WS, class TP, bool kPairs>
-__device__ __forceinline__ void depth_drain(const uint2* __restrict__ queue, int* head, int n,
-                                            const typename WS::T* __restrict__ cur, typename WS::T* __restrict__ nxt,
-                                            const typename TP::E* __restrict__ taps, const float* __restrict__ qs,
-                                            const DepthSeg* __restrict__ segs, int pc, int nk, int lane) {
+__device__ __forceinline__ void depth_drain_items(const uint2* __restrict__ queue, int* head, int n,
+                                                  const typename WS::T* __restrict__ cur,
+                                                  typename WS::T* __restrict__ nxt,
+                                                  const typename TP::E* __restrict__ taps,
+                                                  const float* __restrict__ row, const float* __restrict__ qs,
+                                                  const DepthSeg* __restrict__ segs, int pc, int nk, int lane) {
     if (n <= 0) return;
+    const int r = lane & 7;
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(head, 32);
+        if (lane == 0) base = atomicAdd(head, 4);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) break;
-        const int i = base + lane;
+        const int i = base + (lane >> 3);
         if (i < n) {
             const uint2 e = queue[i];
-            const uint32_t wbo = e.x & 0xffffu;
-            const int sg = (int)((e.x >> 16) & 7u), r = (int)(e.x >> 28);
-            float q;
-            if constexpr (kPairs) q = __int_as_float(segs[sg].line * pc);
-            else q = qs[sg];
-            const int idx = depth_op_index<kPairs>(q, __uint_as_float(e.y), nk);
-            WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)idx * (LT + 1)));
+            if (r > 0 && ((e.x >> (18 + r)) & 1u)) {  // flag bit r (r >= 1) sits at bit 18 + r
+                const uint32_t wbo = e.x & 0xffffu;
+                const int sg = (int)((e.x >> 16) & 7u);
+                float q;
+                if constexpr (kPairs) q = __int_as_float(segs[sg].line * pc);
+                else q = qs[sg];
+                const int idx = depth_op_index<kPairs>(q, row[e.y + r], nk);
+                WS::st1(nxt + wbo + phys(r + LT), fir1<LT, WS, TP>(cur + wbo, r, taps + (size_t)idx * (LT + 1)));
+            }
         }
     }
 }
@@ -495,14 +502,16 @@ __device__ __forceinline__ void depth_mbar_arrive(uint64_t* bar) {
 // fixw) warps or more).
 //
 // With a fixup warp (fixw), the compute warps do not recompute the outputs
-// whose operator differs from their item's: each lane queues them (position,
-// operator) right after its operator analysis, the warp arrives on the queue
-// barrier, and the fixup warp starts computing them (single-output FIRs)
-// while the compute warps run their main FIRs, which leave those outputs
-// unwritten; a compute warp that finds entries in the queue after its main
-// FIR joins the drain, so the queue's tail is spread over the warps that
-// finish first.  The lanes reload the queued outputs into their registers
-// after the step barrier.
+// whose operator differs from their item's: a lane whose item has such
+// outputs queues the item (window base, segment, the flags, its offset in the
+// staged row) right after its operator analysis, the warp arrives on the
+// queue barrier, and the fixup warp starts computing the flagged outputs
+// (single-output FIRs, 8 lanes per item, each taking its output's operator
+// from the staged row) while the compute warps run their main FIRs, which
+// leave those outputs unwritten; a compute warp that finds entries in the
+// queue after its main FIR joins the drain, so the queue's tail is spread over
+// the warps that finish first.  The lanes reload the flagged outputs into
+// their registers after the step barrier.
 template <int LT, class WS, class TP, int NR, bool kPairs, bool kFQ = (NR == 1)>
 __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned char* smem) {
     typedef typename WS::T T;
@@ -664,7 +673,6 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 float qz[NR];
                 int idx0[NR];
                 uint32_t mk[NR];
-                int cnt = 0;
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     qz[k] = qv[k];
@@ -672,29 +680,20 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     idx0[k] = 0;
                     int i1;
                     mk[k] = nv[k] > 0 ? depth_ops<kPairs>(row + ro[k], qz[k], a.nk, nv[k], idx0[k], i1) : 0u;
-                    cnt += __popc(mk[k]);
                 }
-                // queue the flagged outputs: one shared-memory atomic per warp
-                if (__any_sync(0xffffffffu, cnt != 0)) {
-                    int incl = cnt;
+                // queue the items with flagged outputs, one entry per item:
+                // one ballot and one shared-memory atomic per warp and item
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
+                for (int k = 0; k < NR; ++k) {
+                    const uint32_t bal = __ballot_sync(0xffffffffu, mk[k] != 0u);
+                    if (bal) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&qcount[t & 1], __popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (mk[k])
+                            queue[base + __popc(bal & ((1u << lane) - 1u))] =
+                                make_uint2(wb[k] | (sg[k] << 16) | ((mk[k] >> 1) << 19), ro[k]);
                     }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    int base = 0;
-                    if (lane == 31) base = atomicAdd(&qcount[t & 1], total);
-                    int pos = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
-#pragma unroll
-                    for (int k = 0; k < NR; ++k)
-                        if (mk[k]) {
-#pragma unroll
-                            for (int r = 1; r < 8; ++r)
-                                if ((mk[k] >> r) & 1u)
-                                    queue[pos++] = make_uint2(wb[k] | (sg[k] << 16) | ((uint32_t)r << 28),
-                                                              __float_as_uint(row[ro[k] + r]));
-                        }
                 }
                 __syncwarp();
                 if (lane == 0) depth_mbar_arrive(qbar);
@@ -730,8 +729,8 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                     qok = __all_sync(0xffffffffu, mbar_wait_bounded(qbar, (uint32_t)(t & 1), kWaitPolls));
                     if (!qok && lane == 0) atomicOr(a.status, kStatusTimeout);
                     const int nq = __shfl_sync(0xffffffffu, qok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
-                    depth_drain<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], nq, cur, nxt, taps, qs, segs,
-                                                    kPairs ? a.pair_cnt[z] : 0, a.nk, lane);
+                    depth_drain_items<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], nq, cur, nxt, taps, row, qs,
+                                                          segs, kPairs ? a.pair_cnt[z] : 0, a.nk, lane);
                 }
             } else {
 #pragma unroll
@@ -787,8 +786,9 @@ __device__ __forceinline__ void run_depth(const DepthArgs& a, int g, unsigned ch
                 if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
             }
             const int n = __shfl_sync(0xffffffffu, ok ? *reinterpret_cast<volatile int*>(&qcount[t & 1]) : 0, 0);
-            depth_drain<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], n, cur, nxt, taps, qs, segs,
-                                            kPairs ? a.pair_cnt[a.z_begin + t] : 0, a.nk, lane);
+            depth_drain_items<LT, WS, TP, kPairs>(queue, &qcount[2 + (t & 1)], n, cur, nxt, taps,
+                                                  rows + (size_t)(t % kDepthRowSlots) * rowlen, qs, segs,
+                                                  kPairs ? a.pair_cnt[a.z_begin + t] : 0, a.nk, lane);
             if (duty) depth_bulk_wait_read();
             step_barrier();
             if (duty) issue_image(t);
