@@ -231,7 +231,7 @@ def run_reference(args, w):
     return 0
 
 
-def measure_learned(fx, d, b, slab0, steps, flush, train_steps=100000, n_train=8192, seed=2):
+def measure_learned(fx, d, b, slab0, steps, flush, train_steps=1000000, n_train=8192, seed=2, lr=(3e-3, 1e-5)):
     """The learned-operator form on the same inputs: train the operator network
     on the GPU (n_train designed operators at k ~ U[0, k_max], seeded), then
     time fxmig_mlp_migrate + fxmig_image like the plain form."""
@@ -248,7 +248,7 @@ def measure_learned(fx, d, b, slab0, steps, flush, train_steps=100000, n_train=8
     torch.cuda.synchronize()
     t0.record()
     fx.fxmig_design_at(d, k, taps)
-    fx.fxmig_mlp_train(d, params, m, v, 0, train_steps, 3e-3, 1e-5, train_steps, k, taps, ws_t, loss=loss)
+    fx.fxmig_mlp_train(d, params, m, v, 0, train_steps, lr[0], lr[1], train_steps, k, taps, ws_t, loss=loss)
     t1.record()
     torch.cuda.synchronize()
     train_ms = t0.elapsed_time(t1)
@@ -278,7 +278,7 @@ def measure_learned(fx, d, b, slab0, steps, flush, train_steps=100000, n_train=8
         ms.append(e0.elapsed_time(e1))
     l = loss.cpu().numpy()
     return {"ms_per_step": float(np.mean(ms)), "train_ms": train_ms, "train_steps": train_steps,
-            "train_samples": n_train, "train_loss_first_last": [float(l[0]), float(l[-1])],
+            "train_samples": n_train, "train_lr": list(lr), "train_loss_first_last": [float(l[0]), float(l[-1])],
             "image": image.cpu().numpy(), "params": params}
 
 
@@ -960,7 +960,8 @@ def run_native(args, w):
         raise SystemExit(f"unknown forms: {sorted(forms - set(FORM_NAMES))}")
     if world == 1:
         if "learned" in forms and d.L <= 15:
-            learned = measure_learned(fx, d, b, slab0, args.steps, flush, train_steps=args.train_steps)
+            learned = measure_learned(fx, d, b, slab0, args.steps, flush, train_steps=args.train_steps,
+                                      lr=tuple(args.train_lr))
         if "precision" in forms:
             for name in PREC_NAMES:
                 precs[name] = measure_precision(fx, d, b, slab0, args.steps, flush, launch,
@@ -1103,7 +1104,9 @@ def main(argv=None):
                     "storage, per-depth launches, the 8192-trace line, the 64-line batch)")
     ap.add_argument("--forms", default=",".join(FORM_NAMES),
                     help="comma-separated subset of the other forms to run: " + ", ".join(FORM_NAMES))
-    ap.add_argument("--train-steps", type=int, default=100000, help="Adam steps of the operator network")
+    ap.add_argument("--train-steps", type=int, default=1000000, help="Adam steps of the operator network")
+    ap.add_argument("--train-lr", type=float, nargs=2, default=[3e-3, 1e-5], metavar=("MAX", "MIN"),
+                    help="cosine learning-rate schedule of the operator network")
     ap.add_argument("--ref-freqs", type=int, default=24, help="frequencies per oracle step (reference arm)")
     args = ap.parse_args(argv)
     if args.workload == BATCH_NAME:
