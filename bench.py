@@ -487,6 +487,119 @@ def measure_large(fx, flush, steps: int = 3, oracle_check: bool = True):
     return forms
 
 
+# ------------------------------------------------ 3-D, 2-D extrapolators
+FX3D_CHECK_LINES = (0, 35, 70)   # frequency lines of the band migrated by the oracle (all depths, full grid)
+
+
+def ops_per_point_3d(L: int) -> int:
+    """FP32-pipe lane operations per point x frequency of the 2-D stencil:
+    (2L+1)^2 - taps complex additions (orbit sums, 2 lanes each) and taps
+    complex multiply-adds (two packed f32x2 operations, 4 lanes)."""
+    taps = (L + 1) * (L + 2) // 2
+    return 2 * ((2 * L + 1) ** 2 - taps) + 4 * taps
+
+
+def measure_fx3d(fx, flush, steps: int = 3, oracle_check: bool = True):
+    """3-D migration with 2-D extrapolators on the 128 x 128 x 150 layered +
+    lens model (71 frequencies, 13 x 13 stencils): t->f of the flattened
+    section, the 2-D operator table and the image on the GPU; the mean
+    CUDA-event time of fxmig3d_migrate + fxmig3d_image (L2 flushed); and three
+    frequency lines migrated by the GPU and by the FP64 oracle from the same
+    inputs (all depths, the whole grid)."""
+    import torch
+
+    import oracle as O
+    w = W.LAYERED_LENS_3D
+    v, refl = W.layered_lens_model_3d(w)
+    vm = (0.5 * v).astype(np.float32)
+    sec = W.normal_incidence_section_3d(w, v, refl).astype(np.float32)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    k_max = float(om[-1] / float(vm.min()))
+    d = fx.Desc3d(nx=w.nx, ny=w.ny, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz,
+                  dt=w.dt, theta_max_deg=w.theta_deg, k_max=k_max)
+    d2 = fx.flat_desc(d)
+    npts = w.nx * w.ny
+    slab0 = torch.empty((w.nw, npts), dtype=torch.complex64, device="cuda")
+    ws_t = torch.empty(fx.fxmig_workspace_bytes(d2, fx.FXMIG_WS_T2F), dtype=torch.uint8, device="cuda")
+    fx.fxmig_t2f(d2, torch.from_numpy(sec.reshape(npts, w.nt)).cuda(), slab0, ws_t)
+    del ws_t
+    table = torch.empty((w.nk, fx.fxmig3d_num_taps(w.L)), dtype=torch.complex64, device="cuda")
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    fx.fxmig3d_design_operators(d, table)
+    t1.record()
+    torch.cuda.synchronize()
+    design_ms = t0.elapsed_time(t1)
+    vel = torch.from_numpy(vm).cuda()
+    slab = torch.empty_like(slab0)
+    partials = torch.empty((fx.fxmig3d_num_partials(d), w.nz, npts), dtype=torch.float32, device="cuda")
+    ws = torch.empty(fx.fxmig3d_workspace_bytes(d), dtype=torch.uint8, device="cuda")
+    image = torch.empty((w.nz, npts), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = []
+    for it in range(steps + 2):
+        slab.copy_(slab0)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fx.fxmig3d_migrate(d, slab, vel, table, partials, 0, w.nz, ws)
+        fx.fxmig3d_image(d, partials, image)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 2:
+            ms.append(e0.elapsed_time(e1))
+    if fx.fxmig_check(ws) != fx.FXMIG_OK:
+        raise RuntimeError("3-D form: device status " + fx.fxmig_strerror(fx.fxmig_check(ws)))
+    t = float(np.mean(ms))
+    ops = ops_per_point_3d(w.L)
+    peaks, _ = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(0)
+    fp32_peak = props.multi_processor_count * 128 * sm_mhz * 1e6
+    smem_bytes = 8 * (2 * w.L + 1) ** 2            # shared-memory loads of one output (one 8-byte value per tap)
+    smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6   # 128 bytes per cycle and SM
+    out = {"value": w.points / (t * 1e-3), "unit": "point*freq/s", "ms_per_step": t,
+           "what": "3-D f-x migration with 2-D extrapolators (13 x 13 stencils, 28 unique taps, table lookup per "
+                   "point), one launch per depth step; 128 x 128 points x 150 depths x 71 frequencies",
+           "design_ms": design_ms, "ops_per_point": ops,
+           "frac_of_fp32_peak": w.points * ops / (t * 1e-3) / fp32_peak,
+           "smem_bytes_per_point": smem_bytes,
+           "frac_of_smem_bandwidth": w.points * smem_bytes / (t * 1e-3) / smem_peak,
+           "bound": "shared-memory loads (one 8-byte load per stencil tap and output)"}
+    del slab, partials, image, ws
+    if not oracle_check:
+        return out
+    # the oracle on three frequency lines (the GPU migrates the same lines as a problem of their own)
+    lines = list(FX3D_CHECK_LINES)
+    P0 = slab0.cpu().numpy().reshape(w.nw, w.ny, w.nx)[lines]
+    tab = table.cpu().numpy()
+    _, dk = O.k_grid(w.nk, k_max)
+    q = O.q_values(om, dk)[lines]
+    import oracle.fx3d as F
+    ts = time.perf_counter()
+    _, img_ref = F.migrate3d(P0.astype(np.complex128), vm, tab.astype(np.complex128), q)
+    oracle_s = time.perf_counter() - ts
+    errs = []
+    img_sum = np.zeros_like(img_ref)
+    for j, line in enumerate(lines):
+        dj = fx.Desc3d(nx=w.nx, ny=w.ny, nz=w.nz, nt=w.nt, nw=1, i0=w.i0 + line, L=w.L, nk=w.nk, dx=w.dx,
+                       dz=w.dz, dt=w.dt, theta_max_deg=w.theta_deg, k_max=k_max)
+        sl = torch.from_numpy(np.ascontiguousarray(P0[j:j + 1])).cuda()
+        pj = torch.empty((fx.fxmig3d_num_partials(dj), w.nz, npts), dtype=torch.float32, device="cuda")
+        wsj = torch.empty(fx.fxmig3d_workspace_bytes(dj), dtype=torch.uint8, device="cuda")
+        ij = torch.empty((w.nz, npts), dtype=torch.float32, device="cuda")
+        fx.fxmig3d_migrate(dj, sl, vel, table, pj, 0, w.nz, wsj)
+        fx.fxmig3d_image(dj, pj, ij)
+        torch.cuda.synchronize()
+        img_sum += ij.cpu().numpy().reshape(img_ref.shape)
+    err = float(np.linalg.norm(img_sum - img_ref) / np.linalg.norm(img_ref))
+    out.update({"image_rel_l2_vs_fp64_oracle": err,
+                "check": f"frequency lines {lines} of the band, the whole grid and all depths, each migrated "
+                         "by the GPU and by the FP64 oracle (oracle/fx3d.py) with the GPU's table",
+                "oracle_seconds": oracle_s})
+    return out
+
+
 # ------------------------------------------------- the learned form's judge
 LEARNED_WINDOW = (1024, 256)                           # traces of the 2048-trace line (the lens's left edge)
 LEARNED_BLOCKS = ((0, 8), (71, 8), (142, 8), (213, 8))  # frequency blocks (first line, lines) of the band
@@ -866,7 +979,7 @@ def measure_batch_form(fx, flush, steps: int = 3, warmup: int = 3, oracle_check:
 
 
 # ------------------------------------------------------------------ GPU leg
-FORM_NAMES = ("learned", "precision", "per_depth", "large", "batch")
+FORM_NAMES = ("learned", "precision", "per_depth", "large", "batch", "fx3d")
 
 
 def run_native(args, w):
@@ -953,7 +1066,7 @@ def run_native(args, w):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = world * w.points * len(e2e_ms) / (sum(e2e_ms) * 1e-3)
 
-    learned, precs, per_depth, large, batched = None, {}, None, {}, None
+    learned, precs, per_depth, large, batched, fx3d = None, {}, None, {}, None, None
     oracle_leg = not args.no_cpu_baseline and world == 1
     forms = set() if args.no_forms else {f.strip() for f in args.forms.split(",") if f.strip()}
     if forms - set(FORM_NAMES):
@@ -974,6 +1087,8 @@ def run_native(args, w):
                 large = measure_large(fx, flush, oracle_check=oracle_leg)
             if "batch" in forms:
                 batched = measure_batch_form(fx, flush, oracle_check=oracle_leg)
+            if "fx3d" in forms:
+                fx3d = measure_fx3d(fx, flush, oracle_check=oracle_leg)
 
     if rank != 0:
         if world > 1:
@@ -1067,6 +1182,8 @@ def run_native(args, w):
     forms.update(large)
     if batched is not None:
         forms["batched_64"] = batched
+    if fx3d is not None:
+        forms["fx3d_layered_lens_128"] = fx3d
     if forms:
         line["forms"] = forms
     if learned is not None:

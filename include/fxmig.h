@@ -265,6 +265,67 @@ int fxmig_migrate_noalloc(const fxmig_desc *d, void *slab, const float *vel, con
 
 
 /* ------------------------------------------------------------------------
+ * 3-D migration with 2-D extrapolators (Sec. I and Sec. II: explicit f-x
+ * migration extends to 3-D depth migration, where the extrapolator of Eq. 1
+ * becomes a 2-D filter applied by a 2-D convolution over the surface grid,
+ * still frequency by frequency and depth step by depth step; Algorithm 1's
+ * imaging sums the real part over frequencies).
+ *
+ * Grid: nx x ny surface points with one spacing dx in both directions (the
+ * operator's symmetries assume a square grid), nz depth rows of dz.  The
+ * operator is a (2L+1) x (2L+1) stencil with h(i, j) = h(-i, j) = h(i, -j) =
+ * h(j, i), stored as its fxmig3d_num_taps(L) = (L+1)(L+2)/2 unique taps h_p,
+ * p = a (a+1)/2 + b for 0 <= b <= a <= L; tap p multiplies the wavefield summed
+ * over the offsets (+-a, +-b) and (+-b, +-a).  Tables are [nk][taps] complex64
+ * (interleaved re, im), the entry of a point at depth row z and frequency w
+ * chosen as in 2-D: rint_half_even(fl32(q_w fl32(1/v))) clamped to [0, nk-1].
+ * Layouts: wavefield slab [nw][ny][nx] complex64 (x fastest), velocity
+ * [nz][ny][nx] float (the migration velocity, > 0), image [nz][ny][nx] float.
+ * The t->f transform is fxmig_t2f with a 2-D description of nx ny traces
+ * (section [ny][nx][nt]).  The caller owns every buffer; calls are
+ * asynchronous on `stream` and allocate nothing.
+ * ------------------------------------------------------------------------ */
+typedef struct fxmig3d_desc {
+    int nx, ny, nz, nt, nw, i0, L, nk;
+    double dx, dz, dt, theta_max_deg, k_max;   /* as in fxmig_desc; L <= 8 */
+} fxmig3d_desc;
+
+/* Unique taps of a 3-D operator of half-length L, or FXMIG_EINVAL (L > 8). */
+int fxmig3d_num_taps(int L);
+
+/* The 2-D operator table (the 3-D counterpart of fxmig_design_operators):
+ * for k_j = j dk, weighted least squares in FP64 for the unique taps against
+ * exp(i sqrt(k^2 - kx^2 - ky^2) dz) (evanescent exp(-sqrt(kx^2 + ky^2 - k^2)
+ * dz)) on the samples 0 <= ky <= kx <= pi/dx of an M x M grid, M =
+ * max(48, 6 (L+1)), weight 1 where sqrt(kx^2 + ky^2) <= k sin(theta_max) and
+ * 1e-2 elsewhere; then the taps are scaled by 1/max|H| where the response
+ * exceeds 1 on the samples of a 4M x 4M grid.  table [nk][taps] complex64;
+ * table64 optional [nk][taps] complex128.  Errors: FXMIG_EINVAL, FXMIG_ECUDA. */
+int fxmig3d_design_operators(const fxmig3d_desc *d, void *table, void *table64, void *stream);
+
+/* Device workspace of fxmig3d_migrate (256-byte aligned), 0 if d is invalid. */
+size_t fxmig3d_workspace_bytes(const fxmig3d_desc *d);
+
+/* Planes of [nz][ny][nx] floats the image accumulator of fxmig3d_migrate
+ * needs (the 2-D accumulator of the flattened grid), or FXMIG_EINVAL. */
+int fxmig3d_num_partials(const fxmig3d_desc *d);
+
+/* Depth steps [z_begin, z_end) of every frequency plane: slab holds P at
+ * z_begin on entry and at z_end on return; image rows z in [z_begin, z_end)
+ * get the sum over frequencies of Re P before step z, added in fixed point
+ * into `partials` (its rows in that range are cleared first).  One launch per
+ * depth step; `groups` frequency groups per launch (0 = choose).  Errors:
+ * FXMIG_EINVAL (arguments, alignment: slab/table 8 B, partials 16 B, ws 256 B),
+ * FXMIG_ENOSPC (nparts too small), FXMIG_ECUDA.  Device conditions (bad
+ * velocity, fixed-point overflow) are readable with fxmig_check(ws). */
+int fxmig3d_migrate(const fxmig3d_desc *d, void *slab, const float *vel, const void *table, float *partials,
+                    int nparts, int z_begin, int z_end, int groups, void *ws, void *stream);
+
+/* image [nz][ny][nx] float from the accumulator of fxmig3d_migrate.
+ * Errors: FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA. */
+int fxmig3d_image(const fxmig3d_desc *d, const float *partials, int nparts, float *image, void *stream);
+
+/* ------------------------------------------------------------------------
  * Learned operators (extension of Sec. III; the paper designs and stores a
  * table of operators and picks the nearest entry per point).  A network maps
  * x = k / k_max, k = w / v, to the L+1 symmetric complex taps of Eq. 1, so the

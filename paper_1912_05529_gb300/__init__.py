@@ -32,6 +32,8 @@ __all__ = [
     "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials", "fxmig_mlp_migrate",
     "Line", "BatchPlan", "line_of", "fxmig_batch_workspace_bytes", "fxmig_batch_num_partials",
     "fxmig_batch_autotune", "fxmig_migrate_batch",
+    "Desc3d", "fxmig3d_num_taps", "fxmig3d_design_operators", "fxmig3d_workspace_bytes", "fxmig3d_num_partials",
+    "fxmig3d_migrate", "fxmig3d_image", "flat_desc",
 ]
 
 FXMIG_OK, FXMIG_EINVAL, FXMIG_ENOSPC, FXMIG_ECUDA, FXMIG_ETIMEOUT, FXMIG_EVELOCITY, FXMIG_ERANGE = \
@@ -63,6 +65,17 @@ class Desc(ctypes.Structure):
 
     def __repr__(self):
         return "Desc(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
+
+
+class Desc3d(ctypes.Structure):
+    """Mirror of ``fxmig3d_desc`` (3-D migration with 2-D extrapolators)."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int),
+                ("nw", ctypes.c_int), ("i0", ctypes.c_int), ("L", ctypes.c_int), ("nk", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+                ("theta_max_deg", ctypes.c_double), ("k_max", ctypes.c_double)]
+
+    def __repr__(self):
+        return "Desc3d(" + ", ".join(f"{n}={getattr(self, n)}" for n, _ in self._fields_) + ")"
 
 
 class Line(ctypes.Structure):
@@ -129,6 +142,14 @@ def lib():
         L.fxmig_mlp_taps.argtypes = [pd, vp, vp, i, vp, vp]
         L.fxmig_mlp_num_partials.argtypes = [pd]
         L.fxmig_mlp_migrate.argtypes = [pd, vp, vp, vp, vp, i, i, i, vp, sz, vp]
+        p3 = ctypes.POINTER(Desc3d)
+        L.fxmig3d_num_taps.argtypes = [i]
+        L.fxmig3d_design_operators.argtypes = [p3, vp, vp, vp]
+        L.fxmig3d_workspace_bytes.argtypes = [p3]
+        L.fxmig3d_workspace_bytes.restype = sz
+        L.fxmig3d_num_partials.argtypes = [p3]
+        L.fxmig3d_migrate.argtypes = [p3, vp, vp, vp, vp, i, i, i, i, vp, vp]
+        L.fxmig3d_image.argtypes = [p3, vp, i, vp, vp]
         pln, pbp = ctypes.POINTER(Line), ctypes.POINTER(BatchPlan)
         L.fxmig_batch_workspace_bytes.argtypes = [pln, i, i]
         L.fxmig_batch_workspace_bytes.restype = sz
@@ -139,7 +160,8 @@ def lib():
                   "fxmig_image", "fxmig_check", "fxmig_mlp_param_count", "fxmig_design_at",
                   "fxmig_mlp_train", "fxmig_mlp_grad", "fxmig_mlp_taps", "fxmig_mlp_num_partials",
                   "fxmig_mlp_migrate", "fxmig_batch_num_partials", "fxmig_batch_autotune",
-                  "fxmig_migrate_batch", "fxmig_selftest_timeout"):
+                  "fxmig_migrate_batch", "fxmig_selftest_timeout", "fxmig3d_num_taps",
+                  "fxmig3d_design_operators", "fxmig3d_num_partials", "fxmig3d_migrate", "fxmig3d_image"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -261,6 +283,72 @@ def fxmig_image(d: Desc, partials, image, stream=None) -> None:
     nparts = partials.numel() // max(1, d.nz * d.nx)
     ip = _dev_ptr(image, "image", torch.float32, d.nz * d.nx)
     _check(lib().fxmig_image(ctypes.byref(d), pp, int(nparts), ip, _stream(stream)), "fxmig_image")
+
+
+# ------------------------------------------------- 3-D, 2-D extrapolators
+def fxmig3d_num_taps(L: int) -> int:
+    n = lib().fxmig3d_num_taps(int(L))
+    if n < 0:
+        raise FxmigError(n, "fxmig3d_num_taps")
+    return n
+
+
+def flat_desc(d: "Desc3d", L: int = 4) -> Desc:
+    """The 2-D description of the flattened surface grid (nx ny traces), for
+    fxmig_t2f on a section [ny][nx][nt] (the other fields as in d)."""
+    return Desc(nx=d.nx * d.ny, nz=d.nz, nt=d.nt, nw=d.nw, i0=d.i0, L=L, nk=d.nk, dx=d.dx, dz=d.dz, dt=d.dt,
+                theta_max_deg=d.theta_max_deg, k_max=d.k_max)
+
+
+def fxmig3d_design_operators(d: "Desc3d", table, table64=None, stream=None) -> None:
+    """table: [nk][taps] complex64 (device); table64: [nk][taps] complex128 or None."""
+    torch = _torch()
+    n = d.nk * fxmig3d_num_taps(d.L)
+    tp = _dev_ptr(table, "table", torch.float32, 2 * n, complex_ok=True)
+    t64 = None
+    if table64 is not None:
+        if table64.dtype not in (torch.complex128, torch.float64):
+            raise TypeError("table64: expected complex128 or float64")
+        t64 = _dev_ptr(table64, "table64", None, 2 * n)
+    _check(lib().fxmig3d_design_operators(ctypes.byref(d), tp, t64, _stream(stream)), "fxmig3d_design_operators")
+
+
+def fxmig3d_workspace_bytes(d: "Desc3d") -> int:
+    return int(lib().fxmig3d_workspace_bytes(ctypes.byref(d)))
+
+
+def fxmig3d_num_partials(d: "Desc3d") -> int:
+    n = lib().fxmig3d_num_partials(ctypes.byref(d))
+    if n < 0:
+        raise FxmigError(n, "fxmig3d_num_partials")
+    return n
+
+
+def fxmig3d_migrate(d: "Desc3d", slab, vel, table, partials, z_begin, z_end, ws, groups: int = 0,
+                    stream=None) -> None:
+    """slab: [nw][ny][nx] complex64; vel: [nz][ny][nx] float32; table: [nk][taps]
+    complex64; partials: [nparts][nz][ny][nx] float32; ws: uint8 scratch of
+    fxmig3d_workspace_bytes(d)."""
+    torch = _torch()
+    npts = d.nx * d.ny
+    bp = _dev_ptr(slab, "slab", torch.float32, 2 * d.nw * npts, complex_ok=True)
+    vp = _dev_ptr(vel, "vel", torch.float32, d.nz * npts)
+    tp = _dev_ptr(table, "table", torch.float32, 2 * d.nk * fxmig3d_num_taps(d.L), complex_ok=True)
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * npts)
+    wp = _dev_ptr(ws, "ws", None, fxmig3d_workspace_bytes(d) // max(1, ws.element_size()))
+    _check(lib().fxmig3d_migrate(ctypes.byref(d), bp, vp, tp, pp, int(nparts), int(z_begin), int(z_end),
+                                 int(groups), wp, _stream(stream)), "fxmig3d_migrate")
+
+
+def fxmig3d_image(d: "Desc3d", partials, image, stream=None) -> None:
+    """image: [nz][ny][nx] float32 from the accumulator of fxmig3d_migrate."""
+    torch = _torch()
+    npts = d.nx * d.ny
+    pp = _dev_ptr(partials, "partials", torch.float32)
+    nparts = partials.numel() // max(1, d.nz * npts)
+    ip = _dev_ptr(image, "image", torch.float32, d.nz * npts)
+    _check(lib().fxmig3d_image(ctypes.byref(d), pp, int(nparts), ip, _stream(stream)), "fxmig3d_image")
 
 
 def fxmig_check(ws, stream=None) -> int:

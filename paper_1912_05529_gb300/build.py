@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfxmig.so")
 SOURCES = ["api.cu", "migrate.cu", "migrate_rp.cu", "batch.cu", "t2f.cu", "design.cu", "image.cu", "noalloc.cu", "mlp.cu",
-           "mlp_migrate.cu", "status.cu"]
+           "mlp_migrate.cu", "status.cu", "fx3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

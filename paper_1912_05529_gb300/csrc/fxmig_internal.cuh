@@ -291,6 +291,9 @@ cudaError_t launch_batch(const fxmig_line* lines, int n, const fxmig_batch_plan&
 int batch_autotune(const fxmig_line* lines, int n, fxmig_batch_plan* out, void* ws, cudaStream_t s,
                    float* best_ms);
 cudaError_t launch_selftest_timeout(void* ws, int polls, cudaStream_t s);
+// Expand a [nk][L+1] complex64 table into the kernel layout [nk][LT+1] of
+// (hr, hr, hi, hi), zero taps beyond L.
+cudaError_t launch_expand_taps(const float2* table, int nk, int L, int LT, float4* taps, cudaStream_t s);
 cudaError_t launch_image(const fxmig_desc* d, const float* partials, int nparts, float* image,
                          cudaStream_t s);
 

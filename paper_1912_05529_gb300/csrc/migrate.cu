@@ -168,6 +168,13 @@ __global__ void k_expand_taps(const float2* __restrict__ table, int nk, int L, i
     taps[i] = v;
 }
 
+cudaError_t launch_expand_taps(const float2* table, int nk, int L, int LT, float4* taps, cudaStream_t s) {
+    const int n = nk * (LT + 1);
+    if (n == 0) return cudaSuccess;
+    k_expand_taps<<<(n + 255) / 256, 256, 0, s>>>(table, nk, L, LT, taps);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------- host side
 namespace {
 size_t r256(size_t v) { return (v + 255) & ~size_t(255); }

@@ -21,12 +21,13 @@ def fx():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "fxmig.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\s*\*)\s*\*?\s*(fxmig_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\s*\*)\s*\*?\s*(fxmig(?:3d)?_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for n in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_image"):
+    for n in ("fxmig_design_operators", "fxmig_t2f", "fxmig_migrate", "fxmig_image", "fxmig3d_design_operators",
+              "fxmig3d_migrate", "fxmig3d_image"):
         assert n in names
 
 
@@ -225,3 +226,50 @@ def test_selftest_rejects_bad_arguments(fx):
     assert lib.fxmig_selftest_timeout(ctypes.c_void_p((1 << 20) + 8), 100, None) == fx.FXMIG_EINVAL
     assert lib.fxmig_selftest_timeout(ok, 0, None) == fx.FXMIG_EINVAL
     assert lib.fxmig_selftest_timeout(ok, (1 << 20) + 1, None) == fx.FXMIG_EINVAL
+
+
+def _desc3d(fx, **kw):
+    v = dict(nx=40, ny=24, nz=12, nt=128, nw=20, i0=3, L=6, nk=64, dx=20.0, dz=10.0, dt=0.004,
+             theta_max_deg=65.0, k_max=0.2)
+    v.update(kw)
+    return fx.Desc3d(**v)
+
+
+def test_3d_entry_points_reject_bad_arguments(fx):
+    # argument checks only: nothing is enqueued on these paths
+    lib = fx.lib()
+    assert fx.fxmig3d_num_taps(6) == 28 and fx.fxmig3d_num_taps(8) == 45 and fx.fxmig3d_num_taps(0) == 1
+    assert lib.fxmig3d_num_taps(9) == fx.FXMIG_EINVAL and lib.fxmig3d_num_taps(-1) == fx.FXMIG_EINVAL
+    d = _desc3d(fx)
+    nparts = fx.fxmig3d_num_partials(d)
+    assert nparts >= 1
+    need = fx.fxmig3d_workspace_bytes(d)
+    # status head, taps [nk][45 at L = 6 compiled as 6: 28] float4, slowness, norms, second slab
+    assert need >= 256 + 64 * 28 * 16 + 12 * 40 * 24 * 4 + 20 * 8 + 20 * 40 * 24 * 8
+    for bad in (dict(nx=0), dict(ny=0), dict(L=9), dict(nt=1), dict(i0=0), dict(nw=200), dict(dx=0.0),
+                dict(theta_max_deg=95.0)):
+        db = _desc3d(fx, **bad)
+        assert fx.fxmig3d_workspace_bytes(db) == 0, bad
+        assert lib.fxmig3d_num_partials(ctypes.byref(db)) == fx.FXMIG_EINVAL, bad
+        assert lib.fxmig3d_design_operators(ctypes.byref(db), ctypes.c_void_p(1 << 20), None, None) == fx.FXMIG_EINVAL
+    ok = ctypes.c_void_p(1 << 20)
+    mis = ctypes.c_void_p((1 << 20) + 4)
+    assert lib.fxmig3d_design_operators(ctypes.byref(d), None, None, None) == fx.FXMIG_EINVAL
+    assert lib.fxmig3d_design_operators(ctypes.byref(d), mis, None, None) == fx.FXMIG_EINVAL
+    args = dict(slab=ok, vel=ok, table=ok, partials=ok, nparts=nparts, z0=0, z1=d.nz, groups=0, ws=ok)
+
+    def call(**kw):
+        a = dict(args)
+        a.update(kw)
+        return lib.fxmig3d_migrate(ctypes.byref(d), a["slab"], a["vel"], a["table"], a["partials"], a["nparts"],
+                                   a["z0"], a["z1"], a["groups"], a["ws"], None)
+    assert call(slab=None) == fx.FXMIG_EINVAL
+    assert call(vel=None) == fx.FXMIG_EINVAL
+    assert call(ws=mis) == fx.FXMIG_EINVAL
+    assert call(partials=ctypes.c_void_p((1 << 20) + 8)) == fx.FXMIG_EINVAL
+    assert call(z0=5, z1=4) == fx.FXMIG_EINVAL
+    assert call(z1=d.nz + 1) == fx.FXMIG_EINVAL
+    assert call(groups=-1) == fx.FXMIG_EINVAL
+    assert call(nparts=nparts - 1) == fx.FXMIG_ENOSPC
+    assert lib.fxmig3d_image(ctypes.byref(d), ok, nparts - 1, ok, None) == fx.FXMIG_ENOSPC
+    assert lib.fxmig3d_image(ctypes.byref(d), None, nparts, ok, None) == fx.FXMIG_EINVAL

@@ -23,6 +23,8 @@ __all__ = [
     "Workload", "DIFFRACTOR_128", "LAYERED_LENS_2048", "LARGE_8192",
     "band_bins", "ricker", "diffractor_section", "spike_section",
     "layered_lens_model", "normal_incidence_section", "batched_lines",
+    "Workload3d", "DIFFRACTOR_3D", "LAYERED_LENS_3D", "diffractor_section_3d", "spike_section_3d",
+    "layered_lens_model_3d", "normal_incidence_section_3d",
 ]
 
 
@@ -228,3 +230,140 @@ def mlp_init(seed: int = 2, hidden: int = 64, n_out: int = 26, input_scale: floa
         parts.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), (fan_out, fan_in)).ravel())
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts)
+
+
+# ------------------------------------------------------------------ 3-D grids
+@dataclasses.dataclass(frozen=True)
+class Workload3d:
+    """Sizes of one 3-D migration problem: nx x ny surface points with one
+    spacing dx, nz depth rows of dz; the band, L (the 2-D operator's
+    half-length: a (2L+1) x (2L+1) stencil) and the table as in Workload."""
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    nt: int
+    dt: float
+    nz: int
+    dz: float
+    f_lo: float
+    f_hi: float
+    L: int
+    nk: int = 512
+    theta_deg: float = 65.0
+    seed: int = 0
+
+    @property
+    def band(self) -> tuple[int, int]:
+        return band_bins(self.nt, self.dt, self.f_lo, self.f_hi)
+
+    @property
+    def i0(self) -> int:
+        return self.band[0]
+
+    @property
+    def nw(self) -> int:
+        return self.band[1]
+
+    @property
+    def points(self) -> int:
+        return self.nx * self.ny * self.nz * self.nw
+
+
+# Point diffractor in constant velocity on a 40 x 40 grid.
+DIFFRACTOR_3D = Workload3d("diffractor_3d", nx=40, ny=40, dx=20.0, nt=256, dt=0.004, nz=40, dz=10.0,
+                           f_lo=5.0, f_hi=40.0, L=6, nk=256, seed=0)
+# Layered medium with dipping planes and a lens, 128 x 128 points x 150 depths.
+LAYERED_LENS_3D = Workload3d("layered_lens_3d", nx=128, ny=128, dx=20.0, nt=512, dt=0.004, nz=150, dz=10.0,
+                             f_lo=5.0, f_hi=40.0, L=6, nk=512, seed=5)
+
+
+def diffractor_section_3d(w: Workload3d, x0: float, y0: float, z0: float, v: float,
+                          fp: float = 25.0) -> np.ndarray:
+    """Zero-offset section [ny][nx][nt] of one point diffractor (two-way time
+    2 sqrt(z0^2 + r^2) / v, Ricker wavelet, unit amplitude)."""
+    x = np.arange(w.nx) * w.dx
+    y = np.arange(w.ny) * w.dx
+    t = np.arange(w.nt) * w.dt
+    r2 = (x[None, :] - x0) ** 2 + (y[:, None] - y0) ** 2
+    tx = 2.0 * np.sqrt(z0 * z0 + r2) / v
+    return ricker(t[None, None, :] - tx[:, :, None], fp)
+
+
+def spike_section_3d(w: Workload3d, ix: int, iy: int, it: int) -> np.ndarray:
+    """Section [ny][nx][nt] that is zero except d[iy][ix][it] = 1."""
+    d = np.zeros((w.ny, w.nx, w.nt))
+    d[iy, ix, it] = 1.0
+    return d
+
+
+def layered_lens_model_3d(w: Workload3d, n_interfaces: int = 6, v_top: float = 1500.0,
+                          v_range=(1800.0, 4200.0), v_lens: float = 4500.0):
+    """Seeded medium velocity v[nz][ny][nx] (float64, m/s) and reflectivity.
+
+    Planar interfaces z_j(x, y) = z0_j + tan(a_j)(x - X/2) + tan(b_j)(y - Y/2)
+    with z0_j ~ U(0.05, 0.95) Z and a_j, b_j ~ U(-15, 15) degrees; layer 0 has
+    v_top, the layers below U(1800, 4200) m/s.  A lens (ellipsoid with
+    semi-axes X/6, Y/6, Z/8, centre in the middle half laterally and 30-60 %
+    of Z) is blended toward 4500 m/s through its Gaussian-smoothed (sigma = 2
+    samples) indicator.  Reflectivity is +-1 where the layer index changes
+    from the row above.
+    """
+    rng = np.random.default_rng(w.seed)
+    X, Y, Z = w.nx * w.dx, w.ny * w.dx, w.nz * w.dz
+    x = np.arange(w.nx) * w.dx
+    y = np.arange(w.ny) * w.dx
+    z = np.arange(w.nz) * w.dz
+    z0 = rng.uniform(0.05, 0.95, n_interfaces) * Z
+    ta = np.tan(np.radians(rng.uniform(-15.0, 15.0, n_interfaces)))
+    tb = np.tan(np.radians(rng.uniform(-15.0, 15.0, n_interfaces)))
+    vl = np.concatenate([[v_top], rng.uniform(v_range[0], v_range[1], n_interfaces)])
+    zi = z0[:, None, None] + ta[:, None, None] * (x[None, None, :] - X / 2) + tb[:, None, None] * (y[None, :, None] - Y / 2)
+    layer = np.zeros((w.nz, w.ny, w.nx), dtype=np.int64)
+    for j in range(n_interfaces):
+        layer += (zi[j][None, :, :] <= z[:, None, None])
+    v = vl[layer]
+    cx, cy, cz = rng.uniform(0.25, 0.75) * X, rng.uniform(0.25, 0.75) * Y, rng.uniform(0.3, 0.6) * Z
+    ind = ((((x[None, None, :] - cx) / (X / 6)) ** 2 + ((y[None, :, None] - cy) / (Y / 6)) ** 2
+            + ((z[:, None, None] - cz) / (Z / 8)) ** 2) <= 1.0).astype(np.float64)
+    r = 8
+    k = np.exp(-0.5 * (np.arange(-r, r + 1) / 2.0) ** 2)
+    k /= k.sum()
+    s = ind
+    for axis in range(3):
+        pad = [(0, 0)] * 3
+        pad[axis] = (r, r)
+        p = np.pad(s, pad, mode="reflect")
+        acc = np.zeros_like(s)
+        for i in range(2 * r + 1):
+            sl = [slice(None)] * 3
+            sl[axis] = slice(i, i + s.shape[axis])
+            acc += k[i] * p[tuple(sl)]
+        s = acc
+    v = np.clip(v + s * (v_lens - v), v_top, v_lens)
+    change = np.zeros_like(layer, dtype=bool)
+    change[1:] = layer[1:] != layer[:-1]
+    refl = np.where(change, rng.choice([-1.0, 1.0], size=layer.shape), 0.0)
+    return v, refl
+
+
+def normal_incidence_section_3d(w: Workload3d, v: np.ndarray, refl: np.ndarray, fp: float = 25.0,
+                                noise: float = 0.01) -> np.ndarray:
+    """Zero-offset section [ny][nx][nt] from vertical two-way times (as
+    normal_incidence_section, trace by trace), plus Gaussian noise of
+    ``noise`` times the section rms."""
+    rng = np.random.default_rng(w.seed + 7919)
+    T = 2.0 * np.concatenate([np.zeros((1, w.ny, w.nx)), np.cumsum(w.dz / v, axis=0)[:-1]], axis=0)
+    t = np.arange(w.nt) * w.dt
+    d = np.zeros((w.ny, w.nx, w.nt))
+    half = int(math.ceil(0.08 / w.dt))
+    iz, iy, ix = np.nonzero(refl)
+    for zz, yy, xx in zip(iz, iy, ix):
+        c = T[zz, yy, xx]
+        k0 = max(0, int(c / w.dt) - half)
+        k1 = min(w.nt, int(c / w.dt) + half + 1)
+        if k0 < k1:
+            d[yy, xx, k0:k1] += refl[zz, yy, xx] * ricker(t[k0:k1] - c, fp)
+    rms = math.sqrt(float(np.mean(d * d))) or 1.0
+    d += rng.normal(0.0, noise * rms, d.shape)
+    return d
