@@ -15,12 +15,12 @@
 //   octant samples 0 <= ky <= kx <= pi/dx of an M x M grid, weight 1 inside
 //   k sin(theta) and 1e-2 outside, Re and Im separately (Gram matrix,
 //   Cholesky); then the amplitude guard (|H| <= 1) on a 4x finer grid.
-// * k_step3d: one depth step.  A CTA holds a 32 x 8 tile of output points
+// * k_step3d: one depth step.  A CTA holds a 128 x 8 tile of output points
 //   and its halo in shared memory and walks through its group of frequency
-//   planes; a thread computes one output per plane (orbit sums, then packed
-//   f32x2 multiply-adds with the point's taps) and adds the fixed-point image
-//   contribution of its input value over the planes, one reduction per pixel
-//   and CTA.
+//   planes; a thread computes 4 consecutive outputs of a row per plane (row
+//   pairs summed once for the 4, then packed f32x2 multiply-adds with each
+//   point's taps) and adds the fixed-point image contributions of its input
+//   values over the planes, one reduction per pixel and CTA.
 //
 // The image accumulator, its scale and the conversion to an image are those
 // of the 2-D library, applied to the surface grid flattened to nx ny points.
@@ -186,7 +186,9 @@ __global__ void __launch_bounds__(256) k_design2d(double dk, double dx, double d
     }
 }
 
-constexpr int kT3X = 32, kT3Y = 8;  // output tile of a CTA (one output per thread)
+// Output tile of a CTA: 8 rows of 128 points, a thread computing 4
+// consecutive points of one row (kX4), 256 threads.
+constexpr int kX4 = 4, kT3X = 32 * kX4, kT3Y = 8;
 
 struct Step3Args {
     int nx, ny, nw, nk, G, i0, nt, z, pitch;
@@ -200,72 +202,122 @@ struct Step3Args {
     int* status;
 };
 
+// One depth step.  The stencil sum is taken row pair by row pair: for row
+// offset j the thread adds rows y + j and y - j over its window (4 + 2L
+// values, 16-byte loads of value pairs), then every output x takes
+// h(0, j) R(x) + sum_i h(i, j) (R(x + i) + R(x - i)), h(i, j) being unique tap
+// p(max(i, j), min(i, j)).  The tile is stored in groups of 4 values followed
+// by 16 bytes of padding, so that the 16-byte loads of the 32 lanes of a warp
+// (4 values apart) fall into distinct banks.
 template <int LT>
-__global__ void __launch_bounds__(kT3X * kT3Y) k_step3d(const Step3Args a) {
-    constexpr int TW = kT3X + 2 * LT, TH = kT3Y + 2 * LT, NU = (LT + 1) * (LT + 2) / 2;
-    __shared__ __align__(16) float2 tile[TH][TW];
-    const int tx = threadIdx.x % kT3X, ty = threadIdx.x / kT3X;
+__global__ void __launch_bounds__(kT3X / kX4 * kT3Y, 2) k_step3d(const Step3Args a) {
+    static_assert((LT & 1) == 0, "even half-lengths: the window starts on a value pair");
+    constexpr int NW = kX4 + 2 * LT;        // window values of a thread in one row
+    constexpr int TC = kT3X + 2 * LT;       // tile columns
+    constexpr int TH = kT3Y + 2 * LT;       // tile rows
+    constexpr int RS = ((TC + 3) / 4) * 6;  // row stride in values (groups of 4 values + 2 of padding)
+    constexpr int NU = (LT + 1) * (LT + 2) / 2;
+    constexpr int NT = kT3X / kX4 * kT3Y;
+    __shared__ __align__(16) float2 tile[TH * RS];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int tiles_x = (a.nx + kT3X - 1) / kT3X;
     const int x0 = (blockIdx.x % tiles_x) * kT3X, y0 = (blockIdx.x / tiles_x) * kT3Y;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool inside = x < a.nx && y < a.ny;
+    const int xt = x0 + kX4 * tx, y = y0 + ty;
     const int lb = (int)(((long long)blockIdx.y * a.nw) / a.G), le = (int)(((long long)(blockIdx.y + 1) * a.nw) / a.G);
     const size_t plane = (size_t)a.nx * a.ny;
-    const float s = inside ? a.slow[(size_t)a.z * a.pitch + (size_t)y * a.nx + x] : 0.f;
+    bool valid[kX4];
+    float s[kX4];
+#pragma unroll
+    for (int o = 0; o < kX4; ++o) {
+        valid[o] = xt + o < a.nx && y < a.ny;
+        s[o] = valid[o] ? a.slow[(size_t)a.z * a.pitch + (size_t)y * a.nx + xt + o] : 0.f;
+    }
     const float scale = __int_as_float((*a.scale_exp + 127) << 23);
-    long long img = 0;
+    long long img[kX4] = {};
     bool over = false;
-    const u64* t64 = reinterpret_cast<const u64*>(&tile[0][0]);
+    auto tix = [](int r, int c) { return r * RS + (c >> 2) * 6 + (c & 3); };
     for (int l = lb; l < le; ++l) {
-        __syncthreads();  // the previous plane's tile has been read
+        // the plane's tile and halo: every load of the thread issued before
+        // the first store, so that their latencies overlap
         const float2* src = a.in + (size_t)l * plane;
-        for (int e = threadIdx.x; e < TW * TH; e += kT3X * kT3Y) {
-            const int r = e / TW, cc = e - r * TW;
+        constexpr int NL = (TH * TC + NT - 1) / NT;
+        float2 v[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int e = threadIdx.x + k * NT;
+            const int r = e / TC, cc = e - r * TC;
             const int gy = y0 - LT + r, gx = x0 - LT + cc;
-            tile[r][cc] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) ? src[(size_t)gy * a.nx + gx]
-                                                                         : make_float2(0.f, 0.f);
+            v[k] = (e < TH * TC && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) ? src[(size_t)gy * a.nx + gx]
+                                                                                 : make_float2(0.f, 0.f);
+        }
+        __syncthreads();  // the previous plane's tile has been read
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int e = threadIdx.x + k * NT;
+            if (e < TH * TC) tile[tix(e / TC, e % TC)] = v[k];
         }
         __syncthreads();
-        if (!inside) continue;
-        const int cy = ty + LT, cx = tx + LT;
-        auto at = [&](int dy, int dx) { return t64[(cy + dy) * TW + (cx + dx)]; };
-        img += image_fixed(f2_unpack(at(0, 0)).x, scale, over);
         const float q = q_of_line(a.i0, l, a.nt, a.dt, a.dk);
-        const float4* tp = a.taps + (size_t)table_index(q, s, a.nk) * NU;
-        u64 A = 0ull, B = 0ull;
+        const float4* tp[kX4];
 #pragma unroll
-        for (int ta = 0; ta <= LT; ++ta) {
+        for (int o = 0; o < kX4; ++o) tp[o] = a.taps + (size_t)(valid[o] ? table_index(q, s[o], a.nk) : 0) * NU;
+        u64 A[kX4], B[kX4];
+#pragma unroll 1
+        for (int j = 0; j <= LT; ++j) {
+            u64 R[NW];
+            const int rp = ty + LT + j, rm = ty + LT - j;
 #pragma unroll
-            for (int tb = 0; tb <= ta; ++tb) {
-                // the wavefield summed over the orbit of (ta, tb)
-                u64 S;
-                if (ta == 0) {
-                    S = at(0, 0);
-                } else if (tb == 0) {
-                    S = f2_add(f2_add(at(0, ta), at(0, -ta)), f2_add(at(ta, 0), at(-ta, 0)));
-                } else if (ta == tb) {
-                    S = f2_add(f2_add(at(ta, ta), at(ta, -ta)), f2_add(at(-ta, ta), at(-ta, -ta)));
+            for (int t = 0; t < NW / 2; ++t) {
+                const ulonglong2 vp = *reinterpret_cast<const ulonglong2*>(&tile[tix(rp, kX4 * tx + 2 * t)]);
+                if (j == 0) {
+                    R[2 * t] = vp.x;
+                    R[2 * t + 1] = vp.y;
                 } else {
-                    S = f2_add(f2_add(f2_add(at(tb, ta), at(tb, -ta)), f2_add(at(-tb, ta), at(-tb, -ta))),
-                               f2_add(f2_add(at(ta, tb), at(ta, -tb)), f2_add(at(-ta, tb), at(-ta, -tb))));
+                    const ulonglong2 vm = *reinterpret_cast<const ulonglong2*>(&tile[tix(rm, kX4 * tx + 2 * t)]);
+                    R[2 * t] = f2_add(vp.x, vm.x);
+                    R[2 * t + 1] = f2_add(vp.y, vm.y);
                 }
+            }
+            if (j == 0) {
+#pragma unroll
+                for (int o = 0; o < kX4; ++o)
+                    if (valid[o]) img[o] += image_fixed(f2_unpack(R[LT + o]).x, scale, over);
+            }
+#pragma unroll
+            for (int o = 0; o < kX4; ++o) {
+                const int c = LT + o;
                 u64 hr, hi;
-                TapF32::ld(tp + ta * (ta + 1) / 2 + tb, hr, hi);
-                if (ta == 0) {
-                    A = f2_mul(hr, S);
-                    B = f2_mul(hi, S);
+                TapF32::ld(tp[o] + j * (j + 1) / 2, hr, hi);
+                if (j == 0) {
+                    A[o] = f2_mul(hr, R[c]);
+                    B[o] = f2_mul(hi, R[c]);
                 } else {
-                    A = f2_fma(hr, S, A);
-                    B = f2_fma(hi, S, B);
+                    A[o] = f2_fma(hr, R[c], A[o]);
+                    B[o] = f2_fma(hi, R[c], B[o]);
+                }
+#pragma unroll
+                for (int i = 1; i <= LT; ++i) {
+                    const int ta = i > j ? i : j, tb = i > j ? j : i;
+                    TapF32::ld(tp[o] + ta * (ta + 1) / 2 + tb, hr, hi);
+                    const u64 T = f2_add(R[c + i], R[c - i]);
+                    A[o] = f2_fma(hr, T, A[o]);
+                    B[o] = f2_fma(hi, T, B[o]);
                 }
             }
         }
-        const float2 av = f2_unpack(A), bv = f2_unpack(B);
-        a.out[(size_t)l * plane + (size_t)y * a.nx + x] = make_float2(av.x - bv.y, av.y + bv.x);
+        float2* dst = a.out + (size_t)l * plane + (size_t)y * a.nx + xt;
+#pragma unroll
+        for (int o = 0; o < kX4; ++o) {
+            if (!valid[o]) continue;
+            const float2 av = f2_unpack(A[o]), bv = f2_unpack(B[o]);
+            dst[o] = make_float2(av.x - bv.y, av.y + bv.x);
+        }
     }
     if (over) atomicOr(a.status, kStatusOverflow);
-    if (inside && img != 0)
-        atomicAdd(a.acc + (size_t)a.z * a.pitch + acc_slot(y * a.nx + x), (unsigned long long)img);
+#pragma unroll
+    for (int o = 0; o < kX4; ++o)
+        if (valid[o] && img[o] != 0)
+            atomicAdd(a.acc + (size_t)a.z * a.pitch + acc_slot(y * a.nx + xt + o), (unsigned long long)img[o]);
 }
 
 namespace {
@@ -330,7 +382,7 @@ cudaError_t launch_steps(const fxmig3d_desc* d, const Step3Args& base, float2* s
         a.in = bufs[i & 1];
         a.out = bufs[(i + 1) & 1];
         a.z = z_begin + i;
-        k_step3d<LT><<<dim3(tiles, a.G), kT3X * kT3Y, 0, s>>>(a);
+        k_step3d<LT><<<dim3(tiles, a.G), kT3X / kX4 * kT3Y, 0, s>>>(a);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -409,7 +461,14 @@ extern "C" int fxmig3d_migrate(const fxmig3d_desc* d, void* slab, const float* v
             a.acc = reinterpret_cast<unsigned long long*>(partials);
             a.scale_exp = head + kWsScaleExp;
             a.status = head;
-            a.G = groups > 0 ? (groups < d->nw ? groups : d->nw) : (d->nw < 16 ? d->nw : 16);
+            // automatic: enough frequency groups for about four CTAs per SM
+            int sms = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int tiles = ((d->nx + kT3X - 1) / kT3X) * ((d->ny + kT3Y - 1) / kT3Y);
+            const int gauto = (4 * (sms > 0 ? sms : 148) + tiles - 1) / tiles;
+            const int g = groups > 0 ? groups : gauto;
+            a.G = g < 1 ? 1 : (g < d->nw ? g : d->nw);
             float2* sl = static_cast<float2*>(slab);
             switch (LT) {
                 case 2: e = launch_steps<2>(d, a, sl, slab2, z_begin, z_end, s); break;
