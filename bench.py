@@ -491,12 +491,14 @@ def measure_large(fx, flush, steps: int = 3, oracle_check: bool = True):
 FX3D_CHECK_LINES = (0, 35, 70)   # frequency lines of the band migrated by the oracle (all depths, full grid)
 
 
-def ops_per_point_3d(L: int) -> int:
-    """FP32-pipe lane operations per point x frequency of the 2-D stencil:
-    (2L+1)^2 - taps complex additions (orbit sums, 2 lanes each) and taps
-    complex multiply-adds (two packed f32x2 operations, 4 lanes)."""
-    taps = (L + 1) * (L + 2) // 2
-    return 2 * ((2 * L + 1) ** 2 - taps) + 4 * taps
+def ops_per_point_3d(L: int, nx_thread: int = 4) -> int:
+    """FP32-pipe lane operations per point x frequency of the 3-D step as the
+    kernel takes it: the sums of rows y + j and y - j over a thread's window
+    (L (nx_thread + 2L) complex additions shared by its nx_thread points),
+    then per point and row pair L column-pair additions and L + 1 complex
+    multiply-adds (two packed f32x2 operations each)."""
+    f2 = L * (nx_thread + 2 * L) / nx_thread + (L + 1) * L + 2 * (L + 1) ** 2
+    return int(round(2 * f2))
 
 
 def measure_fx3d(fx, flush, steps: int = 3, oracle_check: bool = True):
@@ -556,16 +558,20 @@ def measure_fx3d(fx, flush, steps: int = 3, oracle_check: bool = True):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(0)
     fp32_peak = props.multi_processor_count * 128 * sm_mhz * 1e6
-    smem_bytes = 8 * (2 * w.L + 1) ** 2            # shared-memory loads of one output (one 8-byte value per tap)
+    # shared-memory bytes per output: a thread's 2L + 1 row loads of its
+    # window (4 + 2L values of 8 bytes) for its 4 points, and the tile store
+    smem_bytes = 8 * ((2 * w.L + 1) * (4 + 2 * w.L) / 4.0 + (8 + 2 * w.L) * (128 + 2 * w.L) / 1024.0)
     smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6   # 128 bytes per cycle and SM
     out = {"value": w.points / (t * 1e-3), "unit": "point*freq/s", "ms_per_step": t,
            "what": "3-D f-x migration with 2-D extrapolators (13 x 13 stencils, 28 unique taps, table lookup per "
-                   "point), one launch per depth step; 128 x 128 points x 150 depths x 71 frequencies",
+                   "point), one launch per depth step, 4 points per thread; 128 x 128 points x 150 depths x 71 "
+                   "frequencies",
            "design_ms": design_ms, "ops_per_point": ops,
            "frac_of_fp32_peak": w.points * ops / (t * 1e-3) / fp32_peak,
            "smem_bytes_per_point": smem_bytes,
            "frac_of_smem_bandwidth": w.points * smem_bytes / (t * 1e-3) / smem_peak,
-           "bound": "shared-memory loads (one 8-byte load per stencil tap and output)"}
+           "bound": "latency of the per-plane tile loads and the tap loads (neither the FP32 pipe nor shared "
+                    "memory is saturated; ncu: long-scoreboard stalls first)"}
     del slab, partials, image, ws
     if not oracle_check:
         return out
