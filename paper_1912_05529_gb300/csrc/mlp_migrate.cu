@@ -233,9 +233,10 @@ int plan_mlp_migrate(const fxmig_desc* d, MlpMigratePlan* p) {
     p->groups = p->persistent ? p->pplan.groups : std::max(1, std::min(d->nw, 16));
     p->nparts = image_planes(d->nx);
     // rows per operator block: worst-case operator storage (every point of a
-    // row distinct) of about 2 GiB at most
+    // row distinct) of about 6 GiB at most, and at most the 64 rows one
+    // network launch takes (fewer, longer depth-loop launches)
     const double row_bytes = (double)d->nw * d->nx * (LT + 1) * 16.0;
-    p->zc = (int)std::max(1.0, std::min(64.0, std::floor(2.0 * (double)(1u << 30) / row_bytes)));
+    p->zc = (int)std::max(1.0, std::min(64.0, std::floor(6.0 * (double)(1u << 30) / row_bytes)));
     return FXMIG_OK;
 }
 
