@@ -49,6 +49,29 @@ def reduce_images_rank_order(image, group=None):
     return out
 
 
+def _image_shape(d):
+    """[nz][nx] for a 2-D description, [nz][ny][nx] for a 3-D one."""
+    return (d.nz, d.ny, d.nx) if hasattr(d, "ny") else (d.nz, d.nx)
+
+
+def _migrate3d_on_device(sd, slab, vel, table, launch=None, stream=None):
+    """One rank's block of a 3-D problem through the library (all depth rows
+    of `sd`), then its image (float32 [nz][ny][nx])."""
+    import torch
+
+    import paper_1912_05529_gb300 as fx
+    dev = slab.device
+    partials = torch.empty((fx.fxmig3d_num_partials(sd), sd.nz, sd.ny, sd.nx), dtype=torch.float32, device=dev)
+    ws = torch.zeros(fx.fxmig3d_workspace_bytes(sd), dtype=torch.uint8, device=dev)
+    image = torch.empty((sd.nz, sd.ny, sd.nx), dtype=torch.float32, device=dev)
+    fx.fxmig3d_migrate(sd, slab, vel, table, partials, 0, sd.nz, ws, stream=stream)
+    fx.fxmig3d_image(sd, partials, image, stream)
+    rc = fx.fxmig_check(ws, stream)
+    if rc != fx.FXMIG_OK:
+        raise fx.FxmigError(rc, "fxmig3d_migrate (frequency shard)")
+    return image
+
+
 def _migrate_on_device(sd, slab, vel, table, launch=None, stream=None):
     """One rank's block through the library: the depth loop over all rows of
     `sd` on the rank's lines, then its image (float32 [nz][nx], on the
@@ -74,19 +97,21 @@ def migrate_frequency_shard(d, slab, vel, table, launch=None, group=None, stream
     k_max, first bin i0 + j0) and the images of all ranks are summed in rank
     order on every rank.
 
-    slab       this rank's lines [j0, j0 + n) of the band, [n][nx] complex64
+    slab       this rank's lines [j0, j0 + n) of the band, [n][nx] complex64,
+               or for a 3-D description (Desc3d) its planes [n][ny][nx]
                (device tensor; ignored when the block is empty)
     vel, table the full velocity field and operator table (every rank)
-    migrate_fn (sd, slab, vel, table, launch, stream) -> image [nz][nx]; the
-               library by default
-    Returns the image of the whole band [nz][nx] (same on every rank)."""
+    migrate_fn (sd, slab, vel, table, launch, stream) -> image [nz][nx] (3-D:
+               [nz][ny][nx]); the library by default
+    Returns the image of the whole band (same on every rank)."""
     import torch
     import torch.distributed as dist
     world, rank = dist.get_world_size(group), dist.get_rank(group)
     sd = shard_desc(d, world, rank)
     if sd is None:
         dev = vel.device if hasattr(vel, "device") else "cpu"
-        image = torch.zeros((d.nz, d.nx), dtype=torch.float64 if migrate_fn else torch.float32, device=dev)
+        image = torch.zeros(_image_shape(d), dtype=torch.float64 if migrate_fn else torch.float32, device=dev)
     else:
-        image = (migrate_fn or _migrate_on_device)(sd, slab, vel, table, launch, stream)
+        default = _migrate3d_on_device if hasattr(d, "ny") else _migrate_on_device
+        image = (migrate_fn or default)(sd, slab, vel, table, launch, stream)
     return reduce_images_rank_order(image, group)

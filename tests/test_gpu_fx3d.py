@@ -206,3 +206,23 @@ def test_diffractor_focuses_on_the_gpu(fx, F):
     ref_table = F.design2d_operators(w.nk, k_max, w.dx, w.dz, w.L)
     _, ref = F.migrate3d(P0, vm, ref_table, O.q_values(om, dk))
     assert rel_l2(img, ref) < 1e-4
+
+
+def test_frequency_shards_on_device_sum_to_full_band(fx, F):
+    # the frequency-shard helper's per-rank path for a 3-D description
+    # (shard_desc, the library's depth steps and image on the rank's planes)
+    # for every rank of a 3-way split, summed in rank order, against the
+    # full-band oracle
+    from paper_1912_05529_gb300 import distributed as D
+    w, pr = _case(F, 35, 21, 10, 6)
+    d = _desc(fx, w, pr["k_max"])
+    _, img_ref = F.migrate3d(pr["P0"].astype(np.complex128), pr["vm"], pr["table"].astype(np.complex128), pr["q"])
+    vel, table = _cuda(pr["vm"], torch.float32), _cuda(pr["table"], torch.complex64)
+    total = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device="cuda")
+    for rank in range(3):
+        j0, n = D.frequency_block(w.nw, 3, rank)
+        sd = D.shard_desc(d, 3, rank)
+        assert sd.i0 == d.i0 + j0 and sd.nw == n and sd.k_max == d.k_max and (sd.nx, sd.ny) == (d.nx, d.ny)
+        total += D._migrate3d_on_device(sd, _cuda(pr["P0"][j0:j0 + n], torch.complex64), vel, table)
+    torch.cuda.synchronize()
+    assert rel_l2(total.cpu().numpy(), img_ref) < TOL_IMAGE

@@ -155,3 +155,77 @@ def test_shard_helper_matches_full_band_oracle():
     for _, total, _, _ in res:
         assert np.max(np.abs(total - full)) <= 1e-12 * np.max(np.abs(full))
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def _problem3d():
+    import sys
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    import oracle.fx3d as F
+    import workloads as W
+    w = W.Workload3d("shard3d", nx=20, ny=14, dx=20.0, nt=64, dt=0.004, nz=8, dz=10.0, f_lo=5.0, f_hi=40.0,
+                     L=4, nk=48, seed=6)
+    v, refl = W.layered_lens_model_3d(w)
+    vm = (0.5 * v).astype(np.float32)
+    sec = W.normal_incidence_section_3d(w, v, refl)
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    kmax = float(om[-1] / vm.min())
+    table = F.design2d_operators(w.nk, kmax, w.dx, w.dz, w.L)
+    P0 = O.band_dft(sec.reshape(w.ny * w.nx, w.nt), w.i0, w.nw).reshape(w.nw, w.ny, w.nx)
+    return w, vm, table, kmax, P0
+
+
+def _shard3d_worker(rank, world, port, q):
+    # the shard helper on a 3-D description, the 3-D oracle as the per-rank
+    # depth loop: each rank's block (i0, nw) and the rank-order image sum
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    import oracle as O
+    import oracle.fx3d as F
+    import paper_1912_05529_gb300 as fx
+    from paper_1912_05529_gb300 import distributed as D
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, vm, table, kmax, P0 = _problem3d()
+        d = fx.Desc3d(nx=w.nx, ny=w.ny, nz=w.nz, nt=w.nt, nw=w.nw, i0=w.i0, L=w.L, nk=w.nk, dx=w.dx, dz=w.dz,
+                      dt=w.dt, theta_max_deg=w.theta_deg, k_max=kmax)
+        j0, n = D.frequency_block(w.nw, world, rank)
+
+        def oracle_block(sd, slab, vel, tab, launch, stream):
+            assert (sd.ny, sd.nx) == (w.ny, w.nx) and sd.k_max == kmax
+            om = O.omegas(sd.i0, sd.nw, sd.nt, sd.dt)
+            _, dk = O.k_grid(sd.nk, sd.k_max)
+            _, img = F.migrate3d(slab, vel, tab, O.q_values(om, dk))
+            return torch.from_numpy(img)
+
+        total = D.migrate_frequency_shard(d, P0[j0:j0 + n], vm, table, migrate_fn=oracle_block)
+        q.put((rank, total.numpy(), j0, n))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_helper_3d_matches_full_band_oracle():
+    import oracle as O
+    import oracle.fx3d as F
+    O.build()
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard3d_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w, vm, table, kmax, P0 = _problem3d()
+    om = O.omegas(w.i0, w.nw, w.nt, w.dt)
+    _, dk = O.k_grid(w.nk, kmax)
+    _, full = F.migrate3d(P0, vm, table, O.q_values(om, dk))
+    assert [r[2] for r in res] == [0, res[0][3]] and sum(r[3] for r in res) == w.nw
+    for _, total, _, _ in res:
+        assert total.shape == (w.nz, w.ny, w.nx)
+        assert np.max(np.abs(total - full)) <= 1e-12 * np.max(np.abs(full))
+    assert np.array_equal(res[0][1], res[1][1])
