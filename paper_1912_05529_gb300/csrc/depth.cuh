@@ -29,10 +29,12 @@
 // Compute warps.  Lane item = 8 consecutive outputs of one segment, the same
 // chunks at every step, so a lane keeps its own 8 values in registers and
 // loads only the 2L halo values of its window.  The 8 outputs share the
-// operator of their first point (one tap load per tap); where the slowness
-// changes inside the 8, the flagged outputs are recomputed by a
-// warp-cooperative round of single-output FIRs.  One CTA barrier per step
-// replaces the paper's kernel exit (Sec. III, V).
+// operator of their first point (one tap load per tap); where the operator
+// changes inside the 8, the flagged outputs are recomputed with their own
+// operators by single-output FIRs: queued per item for the fixup warp (and
+// the compute warps that finish first), or, in the forms without a fixup
+// warp, in warp-cooperative rounds.  One CTA barrier per step replaces the
+// paper's kernel exit (Sec. III, V).
 //
 // Imaging.  Every compute lane converts the real parts of its 8 input values
 // to fixed point (2^e scale from a bound on the data) into an imaging buffer
